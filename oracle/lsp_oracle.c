@@ -1,0 +1,646 @@
+/*
+ * lsp_oracle.c -- plain, slow, FP64 CPU oracle for the explicit Hamilton-Jacobi
+ * level-set integrator of "LevelSetPy" (arXiv 2411.03501).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the yardstick the GPU path is judged
+ * against.  It is called from tests/, from the smoke check and from the CPU
+ * baseline leg of the benchmark; the product path never links or calls it, and
+ * it shares no code, header, table or constant with the CUDA sources.
+ *
+ * Everything is written point by point in double precision, in the order the
+ * paper states the method:
+ *   grid + ghost cells          Sec. III-B (grid fields, ghost-cell boundaries)
+ *   one-sided derivatives       Sec. IV-A (Eq. 6, first-order upwinding),
+ *                               Sec. IV-B (Eqs. 8, 11-14, ENO2 / ENO3),
+ *                               Sec. IV-C (Eqs. 15-20, HJ-WENO5)
+ *   Lax-Friedrichs term + GLF   Sec. IV-D, Listing 4 (termLaxFriedrichs,
+ *                               artificialDissipationGLF, partialFunc)
+ *   CFL step                    Sec. IV-D (CFL condition), Sec. V-A
+ *   TVD-RK1/2/3                 Sec. V-A (Eqs. 24-27 and the averaging steps)
+ *   min with target (tube)      Sec. VI-A (variational HJI, Eq. 30)
+ *   Hamiltonians with optimal   Sec. VI-A (Eqs. 31-32: H = -max_u min_d p.f,
+ *   inputs                      closed form with |.| switching terms)
+ *
+ * Where the paper is silent or its printed formulas are garbled, the reading
+ * used is stated at the spot (each one is listed in the design notes).  The
+ * equation numbers are those of the numbered displays of the paper, counted
+ * in order.
+ *
+ * Layout: C order, last axis fastest (the paper: "generalizes a row-major
+ * layout", Sec. III-C).
+ */
+#include <math.h>
+#include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXD 4
+
+/* scheme ids */
+enum { ORC_UPWIND1 = 0, ORC_ENO2 = 1, ORC_ENO3 = 2, ORC_WENO5 = 3 };
+/* dynamics ids */
+enum {
+    ORC_DYN_NORMAL_SPEED = 0, /* H = a |p|                                   */
+    ORC_DYN_TRANSLATE = 1,    /* H = v . p                                   */
+    ORC_DYN_QUADRATIC = 2,    /* H = |p|^2 / 2   (alpha depends on p)        */
+    ORC_DYN_AIR3D = 3,        /* relative pursuit-evasion (x, y, theta)      */
+    ORC_DYN_CAR4D = 4         /* car (x, y, theta, v), reach game            */
+};
+
+typedef struct {
+    int ndim;
+    int scheme;
+    int dyn;
+    int pad_;
+    int64_t n[ORC_MAXD];
+    double lo[ORC_MAXD];
+    double hi[ORC_MAXD];
+    int periodic[ORC_MAXD];
+    double prm[8];
+} orc_problem;
+
+typedef struct {
+    int64_t steps;
+    int64_t stages;
+    double dt_min;
+    double dt_max;
+    double t_end;
+} orc_stats;
+
+/* ------------------------------------------------------------------------ */
+/* Grid (Sec. III-B, Listing 1).                                             */
+/* Reading: a non-periodic axis has nodes lo + i*dx, i = 0..n-1, with        */
+/* dx = (hi-lo)/(n-1); a periodic axis has dx = (hi-lo)/n so that hi itself  */
+/* is the image of lo and is not a node (theta in [0, 2 pi)).                */
+/* ------------------------------------------------------------------------ */
+double orc_dx(const orc_problem* P, int k)
+{
+    if (P->periodic[k]) return (P->hi[k] - P->lo[k]) / (double)P->n[k];
+    return (P->hi[k] - P->lo[k]) / (double)(P->n[k] - 1);
+}
+
+double orc_node(const orc_problem* P, int k, int64_t i)
+{
+    return P->lo[k] + (double)i * orc_dx(P, k);
+}
+
+int64_t orc_npoints(const orc_problem* P)
+{
+    int64_t N = 1;
+    for (int k = 0; k < P->ndim; ++k) N *= P->n[k];
+    return N;
+}
+
+static int64_t stride_of(const orc_problem* P, int k)
+{
+    int64_t s = 1;
+    for (int j = P->ndim - 1; j > k; --j) s *= P->n[j];
+    return s;
+}
+
+/* Ghost width needed by each scheme: the stencils of Sec. IV reach
+ * i-1..i+1 (first order), i-2..i+2 (ENO2), i-3..i+3 (ENO3, WENO5). */
+int orc_ghost_width(int scheme)
+{
+    switch (scheme) {
+    case ORC_UPWIND1: return 1;
+    case ORC_ENO2: return 2;
+    default: return 3;
+    }
+}
+
+/* Fill one extended line u[-G .. n-1+G] (stored at offset G) from the n node
+ * values of a grid line.  Sec. III-B: boundary conditions are "grafted in" by
+ * populating ghost cells.  Periodic: wrap around.  Otherwise (reading; the
+ * paper names no other condition): linear extrapolation from the two nodes
+ * nearest the boundary, u[-k] = u[0] + k (u[0] - u[1]). */
+static void fill_line(const double* line, int64_t n, int G, int periodic, double* ext)
+{
+    for (int64_t i = 0; i < n; ++i) ext[G + i] = line[i];
+    for (int k = 1; k <= G; ++k) {
+        if (periodic) {
+            ext[G - k] = line[((n - k) % n + n) % n];
+            ext[G + n - 1 + k] = line[(k - 1) % n];
+        } else {
+            ext[G - k] = line[0] + (double)k * (line[0] - line[1]);
+            ext[G + n - 1 + k] = line[n - 1] + (double)k * (line[n - 1] - line[n - 2]);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* One-sided derivatives on one extended line.  `u` points at node 0 of the  */
+/* extended line, so u[-G..n-1+G] is valid.  Outputs pm[i] = phi_x^-(x_i),   */
+/* pp[i] = phi_x^+(x_i).  `tie` (nullable) receives, per node, the smallest  */
+/* relative margin of the ENO selections made there (1 when none are made):  */
+/* a margin near zero means a last-bit change of the data can flip the       */
+/* choice of stencil.                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Sec. IV-A, Eq. 6 and the text below it: D^- looks left, D^+ looks right.
+ * (Eq. 6 prints the two labels the other way round; the text fixes the
+ * standard reading: use D^- phi when information travels left to right.) */
+static void upwind1_line(const double* u, int64_t n, double dx, double* pm, double* pp)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        pm[i] = (u[i] - u[i - 1]) / dx;
+        pp[i] = (u[i + 1] - u[i]) / dx;
+    }
+}
+
+/* Divided differences of Sec. IV-B (Eq. 8):
+ *   D1_{j+1/2} = (u_{j+1} - u_j) / dx
+ *   D2_j       = (D1_{j+1/2} - D1_{j-1/2}) / (2 dx)
+ *   D3_{j+1/2} = (D2_{j+1} - D2_j) / (3 dx)                                 */
+static double D1h(const double* u, int64_t j, double dx) /* D1_{j+1/2} */
+{
+    return (u[j + 1] - u[j]) / dx;
+}
+static double D2(const double* u, int64_t j, double dx) /* D2_j */
+{
+    return (D1h(u, j, dx) - D1h(u, j - 1, dx)) / (2.0 * dx);
+}
+static double D3h(const double* u, int64_t j, double dx) /* D3_{j+1/2} */
+{
+    return (D2(u, j + 1, dx) - D2(u, j, dx)) / (3.0 * dx);
+}
+
+static double rel_margin(double a, double b)
+{
+    double s = fabs(a) + fabs(b);
+    if (s == 0.0) return 1.0; /* both zero: either choice gives the same value */
+    return fabs(fabs(a) - fabs(b)) / s;
+}
+
+/* ENO polynomial derivative at node i built on base index k (k = i-1 for the
+ * left derivative, k = i for the right one), Sec. IV-B:
+ *   phi_x(x_i) = Q1'(x_i) + Q2'(x_i) [+ Q3'(x_i)]                (Eq. 10)
+ *   Q1'(x_i)   = D1_{k+1/2}                                          (Eq. 11)
+ *   c          = D2_k if |D2_k| <= |D2_{k+1}| else D2_{k+1}          (Eq. 12)
+ *   Q2'(x_i)   = c (2(i-k) - 1) dx
+ *   c*         = D3_{k*+1/2} if |D3_{k*+1/2}| <= |D3_{k*+3/2}|
+ *                else D3_{k*+3/2}                                    (Eq. 13)
+ *   Q3'(x_i)   = c* (3(i-k*)^2 - 6(i-k*) + 2) dx^2                   (Eq. 14b)
+ * Reading for k* (the paper uses it without defining it; this is the rule of
+ * the Osher-Fedkiw text the paper follows): k* = k-1 when c took D2_k, else
+ * k* = k.  The product in Eq. 14a is read as (x-x_{k*})(x-x_{k*+1})(x-x_{k*+2}),
+ * whose derivative at x_i is the printed Eq. 14b.                           */
+static double eno_at(const double* u, int64_t i, int64_t k, double dx, int order,
+                     double* margin)
+{
+    double q1 = D1h(u, k, dx);
+    double a = D2(u, k, dx), b = D2(u, k + 1, dx);
+    double c;
+    int64_t kstar;
+    if (fabs(a) <= fabs(b)) {
+        c = a;
+        kstar = k - 1;
+    } else {
+        c = b;
+        kstar = k;
+    }
+    double m = rel_margin(a, b);
+    double r = q1 + c * (double)(2 * (i - k) - 1) * dx;
+    if (order >= 3) {
+        double e = D3h(u, kstar, dx), f = D3h(u, kstar + 1, dx);
+        double cs = (fabs(e) <= fabs(f)) ? e : f;
+        double mm = rel_margin(e, f);
+        if (mm < m) m = mm;
+        double s = (double)(i - kstar);
+        r += cs * (3.0 * s * s - 6.0 * s + 2.0) * dx * dx;
+    }
+    if (margin) *margin = m;
+    return r;
+}
+
+static void eno_line(const double* u, int64_t n, double dx, int order, double* pm,
+                     double* pp, double* tie)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double m1, m2;
+        pm[i] = eno_at(u, i, i - 1, dx, order, &m1);
+        pp[i] = eno_at(u, i, i, dx, order, &m2);
+        if (tie) tie[i] = (m1 < m2) ? m1 : m2;
+    }
+}
+
+/* HJ-WENO5 of Sec. IV-C on five first differences v1..v5.
+ *   substencils (Eq. 15):
+ *     phi1 = v1/3 - 7 v2/6 + 11 v3/6
+ *     phi2 = -v2/6 + 5 v3/6 + v4/3
+ *     phi3 = v3/3 + 5 v4/6 - v5/6
+ *   Reading: Eq. 15c is printed with -1/3 on its first term; its coefficients
+ *   must sum to 1 for consistency and only +1/3 reproduces the optimal
+ *   fifth-order combination printed after Eq. 16 with weights (0.1, 0.6, 0.3).
+ *   smoothness (Eq. 18), with sigma2 read as 13/12 (v2 - 2 v3 + v4)^2 +
+ *   1/4 (v2 - v4)^2 (the print repeats the index i-3 in its first bracket):
+ *     s1 = 13/12 (v1 - 2 v2 + v3)^2 + 1/4 (v1 - 4 v2 + 3 v3)^2
+ *     s2 = 13/12 (v2 - 2 v3 + v4)^2 + 1/4 (v2 - v4)^2
+ *     s3 = 13/12 (v3 - 2 v4 + v5)^2 + 1/4 (3 v3 - 4 v4 + v5)^2
+ *   eps (Eq. 19), read with squares: 1e-6 max(v1^2..v5^2) + 1e-99
+ *   alpha (Eq. 17), read with 0.3 on the third weight (the text states the
+ *   optimal weights 0.1, 0.6, 0.3): alpha_k = d_k / (s_k + eps)^2
+ *   w_k = alpha_k / sum alpha (Eq. 20);  result = sum w_k phi_k (Eq. 16).  */
+static double weno5_combine(double v1, double v2, double v3, double v4, double v5)
+{
+    double phi1 = v1 / 3.0 - 7.0 * v2 / 6.0 + 11.0 * v3 / 6.0;
+    double phi2 = -v2 / 6.0 + 5.0 * v3 / 6.0 + v4 / 3.0;
+    double phi3 = v3 / 3.0 + 5.0 * v4 / 6.0 - v5 / 6.0;
+
+    double t;
+    double s1 = 13.0 / 12.0 * (v1 - 2.0 * v2 + v3) * (v1 - 2.0 * v2 + v3);
+    t = v1 - 4.0 * v2 + 3.0 * v3;
+    s1 += 0.25 * t * t;
+    double s2 = 13.0 / 12.0 * (v2 - 2.0 * v3 + v4) * (v2 - 2.0 * v3 + v4);
+    t = v2 - v4;
+    s2 += 0.25 * t * t;
+    double s3 = 13.0 / 12.0 * (v3 - 2.0 * v4 + v5) * (v3 - 2.0 * v4 + v5);
+    t = 3.0 * v3 - 4.0 * v4 + v5;
+    s3 += 0.25 * t * t;
+
+    double mx = v1 * v1;
+    if (v2 * v2 > mx) mx = v2 * v2;
+    if (v3 * v3 > mx) mx = v3 * v3;
+    if (v4 * v4 > mx) mx = v4 * v4;
+    if (v5 * v5 > mx) mx = v5 * v5;
+    double eps = 1e-6 * mx + 1e-99;
+
+    double a1 = 0.1 / ((s1 + eps) * (s1 + eps));
+    double a2 = 0.6 / ((s2 + eps) * (s2 + eps));
+    double a3 = 0.3 / ((s3 + eps) * (s3 + eps));
+    double sum = a1 + a2 + a3;
+    return (a1 / sum) * phi1 + (a2 / sum) * phi2 + (a3 / sum) * phi3;
+}
+
+/* Left derivative: v1..v5 = D+u_{i-3} .. D+u_{i+1} (Sec. IV-C).
+ * Right derivative (reading; the paper gives only the left one): the mirror
+ * image, v1..v5 = D+u_{i+2}, D+u_{i+1}, D+u_i, D+u_{i-1}, D+u_{i-2}.
+ * D+u_j = (u_{j+1} - u_j) / dx.                                            */
+static void weno5_line(const double* u, int64_t n, double dx, double* pm, double* pp)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double d[6]; /* d[m] = D+u_{i-3+m}, m = 0..5 */
+        for (int m = 0; m < 6; ++m) d[m] = (u[i - 3 + m + 1] - u[i - 3 + m]) / dx;
+        pm[i] = weno5_combine(d[0], d[1], d[2], d[3], d[4]);
+        pp[i] = weno5_combine(d[5], d[4], d[3], d[2], d[1]);
+    }
+}
+
+/* Derivatives of phi along `axis` at every node.  pm, pp: N doubles each;
+ * tie (nullable): N doubles, ENO selection margins (1 for non-ENO schemes). */
+int orc_derivs(const orc_problem* P, const double* phi, int axis, double* pm, double* pp,
+               double* tie)
+{
+    if (axis < 0 || axis >= P->ndim) return -1;
+    int G = orc_ghost_width(P->scheme);
+    int64_t n = P->n[axis];
+    if (n < 2 * G + 1) return -2;
+    int64_t s = stride_of(P, axis);
+    int64_t N = orc_npoints(P);
+    int64_t nlines = N / n;
+    double dx = orc_dx(P, axis);
+
+#pragma omp parallel
+    {
+        double* line = (double*)malloc(sizeof(double) * (size_t)n);
+        double* ext = (double*)malloc(sizeof(double) * (size_t)(n + 2 * G));
+        double* lm = (double*)malloc(sizeof(double) * (size_t)n);
+        double* lp = (double*)malloc(sizeof(double) * (size_t)n);
+        double* lt = (double*)malloc(sizeof(double) * (size_t)n);
+#pragma omp for schedule(static)
+        for (int64_t L = 0; L < nlines; ++L) {
+            /* line L: the index with the axis coordinate removed */
+            int64_t outer = L / s, inner = L % s;
+            int64_t base = outer * s * n + inner;
+            for (int64_t i = 0; i < n; ++i) line[i] = phi[base + i * s];
+            fill_line(line, n, G, P->periodic[axis], ext);
+            const double* u = ext + G;
+            for (int64_t i = 0; i < n; ++i) lt[i] = 1.0;
+            switch (P->scheme) {
+            case ORC_UPWIND1: upwind1_line(u, n, dx, lm, lp); break;
+            case ORC_ENO2: eno_line(u, n, dx, 2, lm, lp, lt); break;
+            case ORC_ENO3: eno_line(u, n, dx, 3, lm, lp, lt); break;
+            default: weno5_line(u, n, dx, lm, lp); break;
+            }
+            for (int64_t i = 0; i < n; ++i) {
+                pm[base + i * s] = lm[i];
+                pp[base + i * s] = lp[i];
+                if (tie) tie[base + i * s] = lt[i];
+            }
+        }
+        free(line);
+        free(ext);
+        free(lm);
+        free(lp);
+        free(lt);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hamiltonians (Sec. VI-A pattern: H = -max_u min_d p.f evaluated in closed */
+/* form, the optimal inputs picked by the sign of a costate combination).    */
+/* x: node coordinates, p: costate, d: dimension count.                      */
+/* ------------------------------------------------------------------------ */
+static double ham(const orc_problem* P, const double* x, const double* p)
+{
+    const double* c = P->prm;
+    int d = P->ndim;
+    switch (P->dyn) {
+    case ORC_DYN_NORMAL_SPEED: { /* H = a |p|: fronts move outward at speed a */
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s += p[k] * p[k];
+        return c[0] * sqrt(s);
+    }
+    case ORC_DYN_TRANSLATE: { /* phi_t + v.grad phi = 0 */
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s += c[k] * p[k];
+        return s;
+    }
+    case ORC_DYN_QUADRATIC: {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s += p[k] * p[k];
+        return 0.5 * s;
+    }
+    case ORC_DYN_AIR3D: {
+        /* relative dynamics, evader (control, maximises) turn rate u, pursuer
+         * (disturbance, minimises) turn rate d:
+         *   xdot = -v_e + v_p cos th + u y,  ydot = v_p sin th - u x,
+         *   thdot = d - u.
+         * max_u min_d p.f = p1(-v_e + v_p cos th) + p2 v_p sin th
+         *                   + ue_max |p1 y - p2 x - p3| - ud_max |p3|
+         * and H = -(that), the sign convention of Eq. 31.                 */
+        double ve = c[0], vp = c[1], we = c[2], wp = c[3];
+        double X = x[0], Y = x[1], th = x[2];
+        double v = p[0] * (-ve + vp * cos(th)) + p[1] * vp * sin(th) +
+                   we * fabs(p[0] * Y - p[1] * X - p[2]) - wp * fabs(p[2]);
+        return -v;
+    }
+    case ORC_DYN_CAR4D: {
+        /* xdot = v cos th, ydot = v sin th, thdot = w, vdot = acc; the
+         * control minimises p.f (reach): H = -min_u p.f                     */
+        double wm = c[0], am = c[1];
+        double th = x[2], v = x[3];
+        double m = p[0] * v * cos(th) + p[1] * v * sin(th) - wm * fabs(p[2]) - am * fabs(p[3]);
+        return -m;
+    }
+    }
+    return 0.0;
+}
+
+/* Per-node bound on |dH/dp_k| for the dynamics whose bound does not depend
+ * on p ("partialFunc" of Listing 4).                                        */
+static double partial_bound(const orc_problem* P, const double* x, int k)
+{
+    const double* c = P->prm;
+    switch (P->dyn) {
+    case ORC_DYN_NORMAL_SPEED: return c[0];
+    case ORC_DYN_TRANSLATE: return fabs(c[k]);
+    case ORC_DYN_AIR3D: {
+        double ve = c[0], vp = c[1], we = c[2], wp = c[3];
+        if (k == 0) return fabs(-ve + vp * cos(x[2])) + we * fabs(x[1]);
+        if (k == 1) return vp * fabs(sin(x[2])) + we * fabs(x[0]);
+        return we + wp;
+    }
+    case ORC_DYN_CAR4D: {
+        if (k == 0) return fabs(x[3] * cos(x[2]));
+        if (k == 1) return fabs(x[3] * sin(x[2]));
+        if (k == 2) return c[0];
+        return c[1];
+    }
+    }
+    return 0.0;
+}
+
+static void node_coords(const orc_problem* P, int64_t idx, double* x)
+{
+    for (int k = P->ndim - 1; k >= 0; --k) {
+        int64_t i = idx % P->n[k];
+        idx /= P->n[k];
+        x[k] = orc_node(P, k, i);
+    }
+}
+
+/* Global Lax-Friedrichs coefficients (artificialDissipationGLF, Listing 4;
+ * the paper names the routine without stating it).  Reading: alpha_k is the
+ * maximum over the whole grid of the bound on |dH/dp_k|.  For H = |p|^2/2 the
+ * bound is p-dependent and is taken from the current one-sided derivative
+ * fields: alpha_k = max(|min p_k|, |max p_k|) over p^- and p^+.
+ * pm/pp (ndim arrays of N each) are needed only for that case.             */
+static void alpha_from(const orc_problem* P, double* const* pm, double* const* pp,
+                       double* alpha)
+{
+    int64_t N = orc_npoints(P);
+    for (int k = 0; k < P->ndim; ++k) alpha[k] = 0.0;
+    if (P->dyn == ORC_DYN_QUADRATIC) {
+        for (int k = 0; k < P->ndim; ++k) {
+            double lo = INFINITY, hi = -INFINITY;
+            for (int64_t i = 0; i < N; ++i) {
+                if (pm[k][i] < lo) lo = pm[k][i];
+                if (pm[k][i] > hi) hi = pm[k][i];
+                if (pp[k][i] < lo) lo = pp[k][i];
+                if (pp[k][i] > hi) hi = pp[k][i];
+            }
+            alpha[k] = fmax(fabs(lo), fabs(hi));
+        }
+        return;
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        double x[ORC_MAXD];
+        node_coords(P, i, x);
+        for (int k = 0; k < P->ndim; ++k) {
+            double b = partial_bound(P, x, k);
+            if (b > alpha[k]) alpha[k] = b;
+        }
+    }
+}
+
+/* Lax-Friedrichs numerical Hamiltonian (termLaxFriedrichs, Sec. IV-D and
+ * Listing 4).  Reading of the HJ form (the paper prints only the
+ * conservation-law scheme):
+ *   Hhat(x) = H(x, (p^+ + p^-)/2) - sum_k alpha_k (p^+_k - p^-_k)/2
+ * and the method-of-lines rate (Sec. V-A, Eq. 24) is L = -Hhat.
+ * If alpha_in is NULL alpha is computed from this phi (alpha_out, nullable,
+ * receives it).  rate: N doubles.                                          */
+int orc_rate(const orc_problem* P, const double* phi, const double* alpha_in,
+             double* alpha_out, double* rate)
+{
+    int d = P->ndim;
+    int64_t N = orc_npoints(P);
+    double* pm[ORC_MAXD];
+    double* pp[ORC_MAXD];
+    int rc = 0;
+    for (int k = 0; k < d; ++k) {
+        pm[k] = (double*)malloc(sizeof(double) * (size_t)N);
+        pp[k] = (double*)malloc(sizeof(double) * (size_t)N);
+    }
+    for (int k = 0; k < d && rc == 0; ++k) rc = orc_derivs(P, phi, k, pm[k], pp[k], NULL);
+    if (rc == 0) {
+        double alpha[ORC_MAXD];
+        if (alpha_in) {
+            for (int k = 0; k < d; ++k) alpha[k] = alpha_in[k];
+        } else {
+            alpha_from(P, pm, pp, alpha);
+        }
+        if (alpha_out)
+            for (int k = 0; k < d; ++k) alpha_out[k] = alpha[k];
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < N; ++i) {
+            double x[ORC_MAXD], pbar[ORC_MAXD];
+            node_coords(P, i, x);
+            double diss = 0.0;
+            for (int k = 0; k < d; ++k) {
+                pbar[k] = 0.5 * (pp[k][i] + pm[k][i]);
+                diss += alpha[k] * 0.5 * (pp[k][i] - pm[k][i]);
+            }
+            double hhat = ham(P, x, pbar) - diss;
+            rate[i] = -hhat;
+        }
+    }
+    for (int k = 0; k < d; ++k) {
+        free(pm[k]);
+        free(pp[k]);
+    }
+    return rc;
+}
+
+/* GLF coefficients for the field phi (see alpha_from). */
+int orc_alpha(const orc_problem* P, const double* phi, double* alpha)
+{
+    int d = P->ndim;
+    if (P->dyn != ORC_DYN_QUADRATIC) {
+        alpha_from(P, NULL, NULL, alpha);
+        return 0;
+    }
+    int64_t N = orc_npoints(P);
+    double* pm[ORC_MAXD];
+    double* pp[ORC_MAXD];
+    int rc = 0;
+    for (int k = 0; k < d; ++k) {
+        pm[k] = (double*)malloc(sizeof(double) * (size_t)N);
+        pp[k] = (double*)malloc(sizeof(double) * (size_t)N);
+    }
+    for (int k = 0; k < d && rc == 0; ++k) rc = orc_derivs(P, phi, k, pm[k], pp[k], NULL);
+    if (rc == 0) alpha_from(P, pm, pp, alpha);
+    for (int k = 0; k < d; ++k) {
+        free(pm[k]);
+        free(pp[k]);
+    }
+    return rc;
+}
+
+/* CFL step (Sec. IV-D: lambda max|f'| <= 1; Sec. V-A: adaptive step):
+ *   dt = min(cfl / sum_k(alpha_k / dx_k), t_final - t).                     */
+double orc_cfl_dt(const orc_problem* P, const double* alpha, double cfl, double t,
+                  double t_final)
+{
+    double s = 0.0;
+    for (int k = 0; k < P->ndim; ++k) s += alpha[k] / orc_dx(P, k);
+    double dt = (s > 0.0) ? cfl / s : (t_final - t);
+    if (t_final - t < dt) dt = t_final - t;
+    return dt;
+}
+
+/* One TVD-RK step of size dt (Sec. V-A):
+ *   RK1: phi^{n+1} = phi^n + dt L(phi^n)
+ *   RK2: phi1 = phi^n + dt L(phi^n);  phi^{n+1} = 1/2 (phi^n + phi1 + dt L(phi1))
+ *   RK3: phi1 = phi^n + dt L(phi^n);
+ *        phi2 = 3/4 phi^n + 1/4 (phi1 + dt L(phi1));
+ *        phi^{n+1} = 1/3 phi^n + 2/3 (phi2 + dt L(phi2))
+ * Each stage takes its own GLF coefficients from its own field.  Then, for
+ * a reachable tube (g non-NULL), phi^{n+1} <- min(phi^{n+1}, g) (reading of
+ * the variational inequality of Eq. 30, applied after each full step).
+ * phi is updated in place.                                                */
+int orc_step(const orc_problem* P, double* phi, const double* g, int rk_order, double dt)
+{
+    int64_t N = orc_npoints(P);
+    double* L = (double*)malloc(sizeof(double) * (size_t)N);
+    double* p1 = (double*)malloc(sizeof(double) * (size_t)N);
+    double* p2 = (double*)malloc(sizeof(double) * (size_t)N);
+    int rc = orc_rate(P, phi, NULL, NULL, L);
+    if (rc == 0) {
+        for (int64_t i = 0; i < N; ++i) p1[i] = phi[i] + dt * L[i];
+        if (rk_order == 1) {
+            for (int64_t i = 0; i < N; ++i) phi[i] = p1[i];
+        } else if (rk_order == 2) {
+            rc = orc_rate(P, p1, NULL, NULL, L);
+            for (int64_t i = 0; i < N; ++i) phi[i] = 0.5 * (phi[i] + p1[i] + dt * L[i]);
+        } else {
+            rc = orc_rate(P, p1, NULL, NULL, L);
+            for (int64_t i = 0; i < N; ++i) p2[i] = 0.75 * phi[i] + 0.25 * (p1[i] + dt * L[i]);
+            if (rc == 0) rc = orc_rate(P, p2, NULL, NULL, L);
+            for (int64_t i = 0; i < N; ++i)
+                phi[i] = phi[i] / 3.0 + 2.0 / 3.0 * (p2[i] + dt * L[i]);
+        }
+        if (g)
+            for (int64_t i = 0; i < N; ++i)
+                if (g[i] < phi[i]) phi[i] = g[i];
+    }
+    free(L);
+    free(p1);
+    free(p2);
+    return rc;
+}
+
+/* Integrate from t0 to t_final (odeCFLx of Listing 3): at the start of each
+ * step the GLF coefficients of the current field give dt (FP64, reused by
+ * all stages of the step), the time is accumulated in FP64 and the solve
+ * stops once t >= t_final - 1e-12 |t_final|.  max_steps <= 0: no limit.     */
+int orc_solve(const orc_problem* P, double* phi, const double* g, int rk_order, double cfl,
+              double t0, double t_final, int64_t max_steps, orc_stats* st)
+{
+    double t = t0;
+    int64_t steps = 0;
+    double dtmin = INFINITY, dtmax = 0.0;
+    int rc = 0;
+    while (t < t_final - 1e-12 * fabs(t_final)) {
+        if (max_steps > 0 && steps >= max_steps) break;
+        double alpha[ORC_MAXD];
+        rc = orc_alpha(P, phi, alpha);
+        if (rc) break;
+        double dt = orc_cfl_dt(P, alpha, cfl, t, t_final);
+        if (!(dt > 0.0)) {
+            rc = -3;
+            break;
+        }
+        rc = orc_step(P, phi, g, rk_order, dt);
+        if (rc) break;
+        t += dt;
+        ++steps;
+        if (dt < dtmin) dtmin = dt;
+        if (dt > dtmax) dtmax = dt;
+    }
+    if (st) {
+        st->steps = steps;
+        st->stages = steps * rk_order;
+        st->dt_min = dtmin;
+        st->dt_max = dtmax;
+        st->t_end = t;
+    }
+    return rc;
+}
+
+/* Number of OpenMP threads this build uses (1 without OpenMP). */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Point evaluations, exported for the tests that pin the closed forms:
+ * the Hamiltonian at one state/costate, and the per-node bound on |dH/dp_k|. */
+double orc_ham(const orc_problem* P, const double* x, const double* p)
+{
+    return ham(P, x, p);
+}
+
+double orc_partial_bound(const orc_problem* P, const double* x, int k)
+{
+    return partial_bound(P, x, k);
+}

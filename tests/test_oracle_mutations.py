@@ -1,0 +1,78 @@
+"""The oracle's pins are discriminating: each plausible mistake planted in a
+copy of the oracle source (a flipped sign, a wrong index or coefficient, a
+swapped operand) makes at least one pin in test_oracle_pins.py fail.
+
+Mistakes are planted only in a temporary copy of the C oracle, compiled on
+the CPU; the committed oracle is untouched.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(os.path.dirname(HERE), "oracle", "lsp_oracle.c")
+
+# name -> (text in the oracle, planted replacement)
+MUTANTS = {
+    "weno_substencil3_sign": ("double phi3 = v3 / 3.0 + 5.0", "double phi3 = -v3 / 3.0 + 5.0"),
+    "weno_optimal_weight3": ("double a3 = 0.3 /", "double a3 = 0.1 /"),
+    "weno_sigma2_index": (
+        "double s2 = 13.0 / 12.0 * (v2 - 2.0 * v3 + v4) * (v2 - 2.0 * v3 + v4);",
+        "double s2 = 13.0 / 12.0 * (v2 - 2.0 * v1 + v4) * (v2 - 2.0 * v1 + v4);"),
+    "weno_eps_unsquared": ("double eps = 1e-6 * mx + 1e-99;",
+                           "double eps = 1e-6 * sqrt(mx) + 1e-99;"),
+    "weno_right_not_mirrored": ("pp[i] = weno5_combine(d[5], d[4], d[3], d[2], d[1]);",
+                                "pp[i] = weno5_combine(d[1], d[2], d[3], d[4], d[5]);"),
+    "eno2_selection_flipped": ("if (fabs(a) <= fabs(b)) {", "if (fabs(a) > fabs(b)) {"),
+    "eno3_kstar": ("kstar = k - 1;", "kstar = k;"),
+    "eno3_selection_flipped": ("double cs = (fabs(e) <= fabs(f)) ? e : f;",
+                               "double cs = (fabs(e) <= fabs(f)) ? f : e;"),
+    "eno2_q2_factor": ("double r = q1 + c * (double)(2 * (i - k) - 1) * dx;",
+                       "double r = q1 + c * (double)(2 * (i - k) + 1) * dx;"),
+    "second_difference_factor": ("return (D1h(u, j, dx) - D1h(u, j - 1, dx)) / (2.0 * dx);",
+                                 "return (D1h(u, j, dx) - D1h(u, j - 1, dx)) / (dx);"),
+    "upwind_sides_swapped": (
+        "pm[i] = (u[i] - u[i - 1]) / dx;\n        pp[i] = (u[i + 1] - u[i]) / dx;",
+        "pp[i] = (u[i] - u[i - 1]) / dx;\n        pm[i] = (u[i + 1] - u[i]) / dx;"),
+    "extrapolation_sign": ("ext[G - k] = line[0] + (double)k * (line[0] - line[1]);",
+                           "ext[G - k] = line[0] - (double)k * (line[0] - line[1]);"),
+    "periodic_wrap_off_by_one": ("ext[G + n - 1 + k] = line[(k - 1) % n];",
+                                 "ext[G + n - 1 + k] = line[k % n];"),
+    "dissipation_sign": ("diss += alpha[k] * 0.5 * (pp[k][i] - pm[k][i]);",
+                         "diss -= alpha[k] * 0.5 * (pp[k][i] - pm[k][i]);"),
+    "rk2_average": ("phi[i] = 0.5 * (phi[i] + p1[i] + dt * L[i]);",
+                    "phi[i] = 0.5 * (phi[i] + p1[i]) + dt * L[i];"),
+    "rk3_second_stage": ("p2[i] = 0.75 * phi[i] + 0.25 * (p1[i] + dt * L[i]);",
+                         "p2[i] = 0.5 * phi[i] + 0.5 * (p1[i] + dt * L[i]);"),
+    "cfl_dt_formula": ("s += alpha[k] / orc_dx(P, k);", "s += alpha[k] * orc_dx(P, k);"),
+    "tube_max_instead_of_min": ("if (g[i] < phi[i]) phi[i] = g[i];",
+                                "if (g[i] > phi[i]) phi[i] = g[i];"),
+    "air3d_switching_sign": ("we * fabs(p[0] * Y - p[1] * X - p[2])",
+                             "we * fabs(p[0] * Y + p[1] * X - p[2])"),
+    "air3d_cos_sin": ("p[0] * (-ve + vp * cos(th))", "p[0] * (-ve + vp * sin(th))"),
+    "car4d_bound_axis": ("if (k == 1) return fabs(x[3] * sin(x[2]));",
+                         "if (k == 1) return fabs(x[3] * cos(x[2]));"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    src = open(SRC).read()
+    old, new = MUTANTS[name]
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    c = tmp_path / "mutant.c"
+    c.write_text(src.replace(old, new))
+    so = tmp_path / "mutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", str(c), "-o", str(so), "-lm"],
+                   check=True)
+    r = subprocess.run(
+        [sys.executable, "-m", "pytest", os.path.join(HERE, "test_oracle_pins.py"), "-x", "-q",
+         "-p", "no:cacheprovider"],
+        env=dict(os.environ, LSP_ORACLE_LIB=str(so)), capture_output=True, text=True,
+        timeout=600)
+    assert r.returncode != 0, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
