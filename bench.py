@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark: grid-point updates per second per RK stage of the explicit HJ
+level-set solve on one GB300, with its roofline position and the FP64 oracle
+timed on the host cores beside it.
+
+One benchmark step = one complete reachable-tube solve of the workload
+(phi0 -> t_final: every RK stage of every step, CFL steps, tube), so the
+metric is  points * stages / time.  Default workload: the air3d game at
+201^3 (WENO5, RK3, CFL 0.75, t_final 2.8, FP32; 1747 steps, 5241 stages).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the FP64 oracle on the host cores
+
+Under torchrun (N > 1) every rank solves its own copy of the workload
+(independent replicas: a single solve has no data-parallel split), the
+time is the maximum over ranks, and the value counts every rank's updates.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point updates/s per RK stage"
+UNIT = "updates/s"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB of L2
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload(name: str):
+    from paper_2411_03501_gb300 import workloads as W
+    if name == "air3d_201":
+        spec, phi0, g = W.air3d(n=201)
+    elif name == "car4d_81":
+        spec, phi0, g = W.car4d(n=81)
+    elif name == "normal_speed_2d":
+        spec, phi0, g = W.normal_speed_2d(101)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return spec, phi0, g
+
+
+# Algorithmic work per node per stage (derivation in the design notes).
+#  bytes: stage 1 reads phi and writes W1 (2 words); stage 2 reads W1 and
+#  phi and writes W2 (3); stage 3 reads W2, phi and the target and writes
+#  phi (4): RK3 with a tube averages 3 words per node per stage (RK2 without
+#  a tube: 2.5).  Stencil neighbours and ghost cells are not counted.
+#  flops: FP32 operations of the per-node formulas as the method states them
+#  (FMA = 2, a division = 1, compare/max = 1), with no sharing between
+#  nodes: one-sided derivatives along one axis, both sides (WENO5 156,
+#  ENO3 32, ENO2 15, first order 4); the LF terms of one axis (average
+#  costate 2, dissipation 3); the Hamiltonian (coordinate-only factors such
+#  as sin/cos(theta) excluded); the stage combination with the tube (7).
+DERIV_FLOPS = {"weno5": 156, "eno3": 32, "eno2": 15, "upwind1": 4}
+LF_FLOPS_PER_AXIS = 5
+COMBINE_FLOPS = 7
+
+
+def ham_flops(dyn: str, d: int) -> int:
+    return {"air3d": 15, "car4d": 10, "normal_speed": 2 * d + 1, "translate": 2 * d - 1,
+            "quadratic": 2 * d}[dyn]
+
+
+def algorithmic(spec) -> tuple[float, float]:
+    """(bytes, flops) per node per stage, averaged over the stages of a step."""
+    word = 8 if spec["dtype"] == "f64" else 4
+    rk = spec["rk"]
+    words = {1: 2.0, 2: 2.5, 3: 3.0}[rk]
+    if spec.get("tube"):
+        words += 1.0 / rk
+    d = spec["ndim"]
+    flops = d * (DERIV_FLOPS[spec["scheme"]] + LF_FLOPS_PER_AXIS) + ham_flops(spec["dyn"], d) \
+        + COMBINE_FLOPS
+    return words * word, float(flops)
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    def __init__(self, index: int, path: str):
+        self.index, self.path, self.proc = index, path, None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
+                                          f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_rate(spec, phi0, g, steps: int = 1):
+    """The FP64 oracle as it stands, on the host cores: `steps` full RK steps
+    of the workload from phi0.  Returns (updates/s, seconds, threads)."""
+    import numpy as np
+    import oracle
+    p = np.asarray(phi0, dtype=np.float64)
+    a = oracle.alpha(spec, p)
+    dt = oracle.cfl_dt(spec, a, spec["cfl"], 0.0, spec["t_final"])
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        p = oracle.step(spec, p, dt, spec["rk"], target=g if spec["tube"] else None)
+    el = time.perf_counter() - t0
+    npts = int(np.prod(spec["n"]))
+    return npts * spec["rk"] * steps / el, el, oracle.threads()
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return 0
+    spec, phi0, g = workload(args.workload)
+    import numpy as np
+    npts = int(np.prod(spec["n"]))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(spec, phi0, g, 1)
+    total, t_all, thr = 0.0, 0.0, 1
+    for _ in range(args.steps):
+        _, el, thr = cpu_oracle_rate(spec, phi0, g, 1)
+        t_all += el
+    v = npts * spec["rk"] * args.steps / t_all
+    sample = f"1 RK{spec['rk']} step ({spec['rk']} stages) of {spec['name']} from phi0 per benchmark step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": spec["name"], "points": npts, "parallelism": "replicas",
+                   "l2": "n/a (host)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import numpy as np
+    import torch
+
+    from paper_2411_03501_gb300 import binding as B
+    from paper_2411_03501_gb300 import build as BLD
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0 or not os.path.exists(BLD.LIB):
+        BLD.build()
+    if world > 1:
+        torch.distributed.barrier()
+    spec, phi0, g = workload(args.workload)
+    npts = int(np.prod(spec["n"]))
+    P = B.Problem(spec, use_graph=args.graph)
+    tdt = P.torch_dtype
+    phi0_d = torch.as_tensor(phi0).to("cuda", tdt).contiguous()
+    g_d = torch.as_tensor(g).to("cuda", tdt).contiguous() if g is not None else None
+    phi = torch.empty_like(phi0_d)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one_solve():
+        return P.solve(phi, g_d, 0.0, spec["t_final"])
+
+    # warm-up (also captures the graph when enabled)
+    for _ in range(args.warmup):
+        phi.copy_(phi0_d)
+        stats = one_solve()
+    torch.cuda.synchronize()
+    stages = stats["stages"]
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region: events around each solve, L2
+    # flushed (and phi reset) between solves, outside the events
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clk = ClockSampler(local_rank, os.path.join(args.outdir, f"clocks_rank{rank}.csv"))
+    barrier()
+    with clk:
+        for i in range(args.steps):
+            phi.copy_(phi0_d)
+            flush.zero_()
+            ev[i][0].record(stream)
+            one_solve()
+            ev[i][1].record(stream)
+        barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    tmax = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+    ms = float(tmax.item())
+    units = world * npts * stages * args.steps
+    value = units / (ms / 1e3)
+
+    # ---- end to end through the public API: pinned host inputs copied in,
+    # the solve, the result copied out, all inside the timed region
+    h_phi0 = torch.as_tensor(phi0).to(tdt).pin_memory()
+    h_g = torch.as_tensor(g).to(tdt).pin_memory() if g is not None else None
+    h_out = torch.empty_like(h_phi0).pin_memory()
+    d_g = torch.empty_like(g_d) if g_d is not None else None
+    bi = h_phi0.numel() * h_phi0.element_size() + (h_g.numel() * h_g.element_size() if h_g is not None else 0)
+    bo = h_out.numel() * h_out.element_size()
+
+    def e2e_step():
+        phi.copy_(h_phi0, non_blocking=True)
+        if h_g is not None:
+            d_g.copy_(h_g, non_blocking=True)
+        P.solve(phi, d_g, 0.0, spec["t_final"])
+        h_out.copy_(phi, non_blocking=True)
+
+    if args.graph:
+        # the graph was captured for g_d; the e2e leg uses its own target buffer
+        P_e2e = B.Problem(spec, use_graph=True)
+
+        def e2e_step():  # noqa: F811
+            phi.copy_(h_phi0, non_blocking=True)
+            if h_g is not None:
+                d_g.copy_(h_g, non_blocking=True)
+            P_e2e.solve(phi, d_g, 0.0, spec["t_final"])
+            h_out.copy_(phi, non_blocking=True)
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    barrier()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev2[i][0].record(stream)
+        e2e_step()
+        ev2[i][1].record(stream)
+    barrier()
+    ms2 = sum(a.elapsed_time(b) for a, b in ev2)
+    t2 = torch.tensor([ms2], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t2, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = units / (float(t2.item()) / 1e3)
+
+    if rank != 0:
+        return 0
+
+    # ---- roofline of the dominant kernel (the fused stage kernel): its
+    # average launch time over the timed region = solve time / stage launches
+    peaks, src = _peaks()
+    per_launch_s = (ms / 1e3) / (stages * args.steps)
+    bpn, fpn = algorithmic(spec)
+    hbm_ach = bpn * npts / per_launch_s / 1e9
+    flop_ach = fpn * npts / per_launch_s / 1e12
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes, TFLOP/s
+    hbm_peak = float(peaks["hbm_gbs"])
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", f"traffic_{spec['name']}.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            traffic = json.load(f).get("bytes_per_launch")
+    alu = {"bound": "alu", "achieved": flop_ach, "peak": alu_peak, "unit": "TFLOP/s",
+           "frac": flop_ach / alu_peak, "traffic": traffic,
+           "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock"}
+    hbm = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
+           "frac": hbm_ach / hbm_peak, "traffic": traffic,
+           "peak_note": f"{src} STREAM copy"}
+    roof = dict(alu if alu["frac"] >= hbm["frac"] else hbm)
+    roof["other"] = hbm if roof["bound"] == "alu" else alu
+
+    # ---- the oracle on this host's cores: a bounded sample of the workload
+    cpu = None
+    if args.cpu_baseline:
+        v, el, thr = cpu_oracle_rate(spec, phi0, g, 1)
+        cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"1 RK{spec['rk']} step ({spec['rk']} stages, {el:.1f} s) of "
+                         f"{spec['name']} from phi0, FP64, OpenMP over {thr} threads"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": spec["dtype"], "data": "synthetic",
+        "config": {"workload": spec["name"], "points": npts, "stages_per_step": stages,
+                   "rk_steps_per_step": stats["steps"], "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed (512 MB write) between timed solves",
+                   "graph": bool(args.graph)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
+                "d2h_bytes_per_step": bo},
+        "gpu_launches": stages * args.steps,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="air3d_201")
+    ap.add_argument("--graph", type=int, default=0)
+    ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--outdir", default=os.path.join(ROOT, "gpurun_out"))
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    os.makedirs(args.outdir, exist_ok=True)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * lsp.h -- C ABI of the GB300 (sm_103a) explicit Hamilton-Jacobi level-set
+ * integrator.  The method is the one of "LevelSetPy" (arXiv 2411.03501):
+ * explicit integration of  phi_t + H(x, grad phi) = 0  (Eq. 1) on a dense
+ * Cartesian grid with ghost-cell boundaries (Sec. III-B), upwind ENO/WENO
+ * one-sided derivatives (Sec. IV-A..IV-C), the Lax-Friedrichs numerical
+ * Hamiltonian with global-LF dissipation (Sec. IV-D, Listing 4), a CFL time
+ * step (Sec. IV-D, V-A), TVD-RK1/2/3 (Sec. V-A) and, for reachable tubes,
+ * the minimum with the target after each step (Sec. VI-A, Eq. 30).
+ *
+ * Conventions shared by every call:
+ *  - Fields are dense C-order arrays (last axis fastest) of n[0]*...*n[d-1]
+ *    elements of the solve's dtype (float or double), in DEVICE memory of the
+ *    current CUDA device, 16-byte aligned.  The caller owns every field and
+ *    every workspace; the library owns only its opaque handles and never
+ *    allocates device memory inside a step or a solve.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it; calls return without waiting for the
+ *    GPU unless stated otherwise.
+ *  - Sign convention: phi_t + H = 0 integrated forward in time-to-go.
+ *    Reachability Hamiltonians are H = -max_u min_d p.f (Eq. 31).
+ *  - Every call returns an lsp_status and never aborts the process.  The
+ *    text of the last error of the calling thread is in lsp_last_error().
+ *    Asynchronous CUDA errors surface as LSP_ECUDA on a later call.
+ *  - Device-side failures (non-finite values produced) set a flag in the
+ *    workspace; they are reported when the call waits for the GPU
+ *    (lsp_solve_opts.check_finite) or by lsp_check_status().
+ */
+#ifndef LSP_H
+#define LSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LSP_OK = 0,
+    LSP_EINVAL = 1,       /* bad argument (described by lsp_last_error)      */
+    LSP_ENOMEM = 2,       /* workspace too small                             */
+    LSP_ECUDA = 3,        /* a CUDA runtime error                            */
+    LSP_EUNSUPPORTED = 4, /* combination not provided                       */
+    LSP_ENONFINITE = 5,   /* a NaN or infinity was produced                  */
+    LSP_ETIMEOUT = 6      /* a bounded device-side wait gave up              */
+} lsp_status;
+
+/* Boundary condition of one axis (Sec. III-B: boundary conditions are set
+ * by populating ghost cells).  PERIODIC wraps around (the axis' upper bound
+ * is then the image of the lower one and is not a node).  EXTRAPOLATE fills
+ * ghost cells by linear extrapolation from the two nodes nearest the
+ * boundary. */
+typedef enum { LSP_BC_EXTRAPOLATE = 0, LSP_BC_PERIODIC = 1 } lsp_bc;
+
+/* One-sided derivative approximation (the CoStateCalc of Listing 4):
+ * first-order upwinding (Sec. IV-A), ENO2 and ENO3 (Sec. IV-B), HJ-WENO5
+ * (Sec. IV-C).  Ghost widths 1, 2, 3, 3. */
+typedef enum { LSP_UPWIND1 = 0, LSP_ENO2 = 1, LSP_ENO3 = 2, LSP_WENO5 = 3 } lsp_scheme;
+
+/* Dynamics (hamFunc + partialFunc of Listing 4).  Parameters:
+ *  NORMAL_SPEED  any d   H = a |p|                            {a}
+ *  TRANSLATE     any d   H = v . p                            {v_0..v_{d-1}}
+ *  QUADRATIC     any d   H = |p|^2 / 2 (LF bound from p)      {}
+ *  AIR3D         d = 3   relative pursuit-evasion (x, y, theta); evader
+ *                        turn rate u maximises, pursuer turn rate d
+ *                        minimises; H = -max_u min_d p.f      {v_e, v_p, u_max, d_max}
+ *  CAR4D         d = 4   car (x, y, theta, v), turn rate and
+ *                        acceleration minimise p.f (reach)     {w_max, a_max}
+ */
+typedef enum {
+    LSP_DYN_NORMAL_SPEED = 0,
+    LSP_DYN_TRANSLATE = 1,
+    LSP_DYN_QUADRATIC = 2,
+    LSP_DYN_AIR3D = 3,
+    LSP_DYN_CAR4D = 4
+} lsp_dyn;
+
+typedef enum { LSP_F32 = 0, LSP_F64 = 1 } lsp_dtype;
+
+typedef struct lsp_grid lsp_grid; /* opaque: grid + dynamics */
+
+/* Options of a step or a solve (the odeCFLx options of Listing 3). */
+typedef struct {
+    int rk_order;      /* 1, 2 or 3 (TVD-RK, Sec. V-A)                     */
+    int scheme;        /* lsp_scheme                                       */
+    int dtype;         /* lsp_dtype of phi, target and the workspace fields */
+    int tube;          /* 1: phi <- min(phi, target) after every step      */
+    double cfl;        /* CFL number in (0, 1]                             */
+    int check_finite;  /* 1: wait for the GPU at the end of the call and
+                          return LSP_ENONFINITE if a non-finite value was
+                          produced                                         */
+    int use_graph;     /* 1: lsp_hj_solve replays its launches as a CUDA
+                          graph (captured on the first call with the same
+                          arguments, kept in the grid handle)              */
+    int reserved[6];   /* must be zero                                     */
+} lsp_solve_opts;
+
+typedef struct {
+    int64_t steps;     /* RK steps taken                                   */
+    int64_t stages;    /* stage evaluations (steps * rk_order)             */
+    double dt_min;     /* smallest and largest step                        */
+    double dt_max;
+    double t_end;      /* time reached (FP64 accumulator)                  */
+} lsp_solve_stats;
+
+/* Create a grid (createGrid(gmin, gmax, N, pdim) of Listing 1).
+ *  ndim      1..4
+ *  gmin/gmax ndim lower / upper bounds (host), finite, gmax > gmin
+ *  n         ndim node counts (host), each >= 7 (room for a 3-cell stencil)
+ *  bc        ndim boundary conditions (host), lsp_bc values
+ * Spacing: (gmax-gmin)/(n-1) on non-periodic axes, (gmax-gmin)/n on periodic
+ * ones.  *out receives a handle to be released with lsp_grid_destroy.
+ * Errors: LSP_EINVAL on a bad argument; nothing is allocated then. */
+lsp_status lsp_grid_create(int ndim, const double* gmin, const double* gmax, const int64_t* n,
+                           const int* bc, lsp_grid** out);
+
+/* Release a grid and anything cached in it (captured graphs).  NULL is a
+ * no-op. */
+void lsp_grid_destroy(lsp_grid* grid);
+
+/* Attach dynamics to a grid (the hamFunc / partialFunc / dissFunc triple of
+ * Listing 4).  params: nparams doubles (host), see lsp_dyn.  For dynamics
+ * whose bound on |dH/dp_k| depends on the state only, the global-LF
+ * coefficients alpha_k = max over the grid nodes of that bound are computed
+ * here on the current device (a reduction kernel; the call waits for it).
+ * Errors: LSP_EINVAL (wrong parameter count, dimension mismatch, non-finite
+ * parameter), LSP_ECUDA. */
+lsp_status lsp_set_dynamics(lsp_grid* grid, int dyn, const double* params, int nparams);
+
+/* The global-LF coefficients alpha_k (host, ndim doubles) found by
+ * lsp_set_dynamics.  LSP_EUNSUPPORTED for QUADRATIC (its alpha depends on
+ * phi and is recomputed on the device at every stage). */
+lsp_status lsp_get_alpha(const lsp_grid* grid, double* alpha);
+
+/* Bytes of device workspace a step or solve with these options needs: two
+ * stage fields (one for RK1/RK2) plus a 256-byte control block. */
+lsp_status lsp_workspace_size(const lsp_grid* grid, const lsp_solve_opts* opts, size_t* bytes);
+
+/* The CFL step of Sec. IV-D / V-A for time t:
+ *   dt = min(cfl / sum_k(alpha_k / dx_k), t_final - t)   (FP64, host)
+ * Not available for QUADRATIC (LSP_EUNSUPPORTED). */
+lsp_status lsp_cfl_dt(const lsp_grid* grid, const lsp_solve_opts* opts, double t,
+                      double t_final, double* dt);
+
+/* Method-of-lines rate L(phi) = -Hhat at every node (Sec. IV-D and V-A):
+ *   Hhat = H(x, (p^+ + p^-)/2) - sum_k alpha_k (p^+_k - p^-_k) / 2
+ * with p^-/p^+ from opts->scheme and alpha the global-LF coefficients.
+ * phi (in), rate (out): device fields of opts->dtype.  Uses the workspace
+ * control block.  Asynchronous. */
+lsp_status lsp_hj_rate(lsp_grid* grid, const lsp_solve_opts* opts, const void* phi, void* rate,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* One TVD-RK step (Sec. V-A) of phi in place, followed, if opts->tube, by
+ * phi <- min(phi, target) (Sec. VI-A).  Each stage is one fused kernel:
+ * ghost cells, derivatives, Hamiltonian + LF, RK combination (and the
+ * minimum with the target in the last stage).
+ *  phi       device field, in/out
+ *  target    device field (read if opts->tube, else may be NULL)
+ *  t         time of phi (only for the CFL step)
+ *  dt_io     in: step size if *dt_io > 0; if *dt_io <= 0 the CFL step for
+ *            t_final = +inf is used and written back (not for QUADRATIC,
+ *            whose step the device computes; *dt_io then must be <= 0 and
+ *            receives the step after waiting for the GPU).
+ * Errors: LSP_EINVAL, LSP_ENOMEM (workspace too small), LSP_ECUDA,
+ * LSP_ENONFINITE (only with opts->check_finite). */
+lsp_status lsp_hj_step(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
+                       const void* target, double t, double* dt_io, void* workspace,
+                       size_t workspace_bytes, void* stream);
+
+/* Integrate phi in place from t0 to t_final (odeCFLx of Listing 3): CFL
+ * steps of dt = min(cfl / sum_k alpha_k/dx_k, t_final - t), the time kept
+ * in FP64, stopping once t >= t_final - 1e-12 |t_final|.  Arguments as for
+ * lsp_hj_step; stats (host, nullable) receives the step count and range.
+ * For state-only bounds the step sequence is known on the host, so the
+ * call only enqueues work (or replays a captured graph with
+ * opts->use_graph).  For QUADRATIC it waits for the GPU once per step. */
+lsp_status lsp_hj_solve(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
+                        const void* target, double t0, double t_final, void* workspace,
+                        size_t workspace_bytes, lsp_solve_stats* stats, void* stream);
+
+/* Wait for `stream` and report a device-side failure flagged in the
+ * workspace control block since the last call that reset it (every step
+ * and solve resets it on entry).  LSP_OK, LSP_ENONFINITE or LSP_ECUDA. */
+lsp_status lsp_check_status(const void* workspace, void* stream);
+
+/* Text for a status code; thread-local text of the last error. */
+const char* lsp_status_string(lsp_status s);
+const char* lsp_last_error(void);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int lsp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSP_H */

@@ -1,0 +1,244 @@
+"""Thin ctypes binding of the C ABI in ``include/lsp.h``.
+
+Functions keep the C names and only marshal arguments: torch tensors become
+device pointers, the current torch CUDA stream becomes the ``stream``
+argument, and a non-OK status raises :class:`LspError` with the library's
+error text.  Every step of the computation runs in the CUDA library; if it
+has not been built, the first call raises (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "liblsp.so")
+
+LSP_OK, LSP_EINVAL, LSP_ENOMEM, LSP_ECUDA, LSP_EUNSUPPORTED, LSP_ENONFINITE, LSP_ETIMEOUT = range(7)
+BC = {"extrapolate": 0, "periodic": 1}
+SCHEMES = {"upwind1": 0, "eno2": 1, "eno3": 2, "weno5": 3}
+DYNAMICS = {"normal_speed": 0, "translate": 1, "quadratic": 2, "air3d": 3, "car4d": 4}
+DTYPES = {"f32": 0, "f64": 1}
+
+# Every symbol the header declares (checked by the ABI test).
+EXPORTS = [
+    "lsp_version", "lsp_status_string", "lsp_last_error", "lsp_grid_create", "lsp_grid_destroy",
+    "lsp_set_dynamics", "lsp_get_alpha", "lsp_workspace_size", "lsp_cfl_dt", "lsp_hj_rate",
+    "lsp_hj_step", "lsp_hj_solve", "lsp_check_status",
+]
+
+
+class LspError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lsp status {status}: {msg}")
+        self.status = status
+
+
+class lsp_solve_opts(ctypes.Structure):
+    _fields_ = [
+        ("rk_order", ctypes.c_int),
+        ("scheme", ctypes.c_int),
+        ("dtype", ctypes.c_int),
+        ("tube", ctypes.c_int),
+        ("cfl", ctypes.c_double),
+        ("check_finite", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+        ("reserved", ctypes.c_int * 6),
+    ]
+
+
+class lsp_solve_stats(ctypes.Structure):
+    _fields_ = [
+        ("steps", ctypes.c_int64),
+        ("stages", ctypes.c_int64),
+        ("dt_min", ctypes.c_double),
+        ("dt_max", ctypes.c_double),
+        ("t_end", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load liblsp.so (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(path)
+    vp, sz = ctypes.c_void_p, ctypes.c_size_t
+    dp = ctypes.POINTER(ctypes.c_double)
+    op = ctypes.POINTER(lsp_solve_opts)
+    L.lsp_version.restype = ctypes.c_int
+    L.lsp_status_string.argtypes = [ctypes.c_int]
+    L.lsp_status_string.restype = ctypes.c_char_p
+    L.lsp_last_error.restype = ctypes.c_char_p
+    L.lsp_grid_create.argtypes = [ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp)]
+    L.lsp_grid_destroy.argtypes = [vp]
+    L.lsp_grid_destroy.restype = None
+    L.lsp_set_dynamics.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int]
+    L.lsp_get_alpha.argtypes = [vp, dp]
+    L.lsp_workspace_size.argtypes = [vp, op, ctypes.POINTER(sz)]
+    L.lsp_cfl_dt.argtypes = [vp, op, ctypes.c_double, ctypes.c_double, dp]
+    L.lsp_hj_rate.argtypes = [vp, op, vp, vp, vp, sz, vp]
+    L.lsp_hj_step.argtypes = [vp, op, vp, vp, ctypes.c_double, dp, vp, sz, vp]
+    L.lsp_hj_solve.argtypes = [vp, op, vp, vp, ctypes.c_double, ctypes.c_double, vp, sz,
+                               ctypes.POINTER(lsp_solve_stats), vp]
+    L.lsp_check_status.argtypes = [vp, vp]
+    for name in ("lsp_grid_create", "lsp_set_dynamics", "lsp_get_alpha", "lsp_workspace_size",
+                 "lsp_cfl_dt", "lsp_hj_rate", "lsp_hj_step", "lsp_hj_solve", "lsp_check_status"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != LSP_OK:
+        raise LspError(status, load().lsp_last_error().decode())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _nbytes(t) -> int:
+    return t.numel() * t.element_size()
+
+
+class Grid:
+    """Owning wrapper of an ``lsp_grid*`` (destroyed with the object)."""
+
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.lsp_grid_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+
+def lsp_version() -> int:
+    return int(load().lsp_version())
+
+
+def lsp_grid_create(ndim, gmin, gmax, n, bc) -> Grid:
+    D = ctypes.c_double * ndim
+    out = ctypes.c_void_p()
+    bcs = [BC[b] if isinstance(b, str) else int(b) for b in bc]
+    _check(load().lsp_grid_create(ndim, D(*gmin), D(*gmax), (ctypes.c_int64 * ndim)(*n),
+                                  (ctypes.c_int * ndim)(*bcs), ctypes.byref(out)))
+    return Grid(out.value)
+
+
+def lsp_set_dynamics(grid: Grid, dyn, params):
+    d = DYNAMICS[dyn] if isinstance(dyn, str) else int(dyn)
+    arr = (ctypes.c_double * max(1, len(params)))(*params)
+    _check(load().lsp_set_dynamics(grid.handle, d, arr, len(params)))
+
+
+def lsp_get_alpha(grid: Grid, ndim: int):
+    a = (ctypes.c_double * 4)()
+    _check(load().lsp_get_alpha(grid.handle, a))
+    return [a[k] for k in range(ndim)]
+
+
+def make_opts(rk_order=3, scheme="weno5", dtype="f32", tube=False, cfl=0.75, check_finite=False,
+              use_graph=False) -> lsp_solve_opts:
+    o = lsp_solve_opts()
+    o.rk_order = int(rk_order)
+    o.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    o.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    o.tube = 1 if tube else 0
+    o.cfl = float(cfl)
+    o.check_finite = 1 if check_finite else 0
+    o.use_graph = 1 if use_graph else 0
+    return o
+
+
+def lsp_workspace_size(grid: Grid, opts: lsp_solve_opts) -> int:
+    b = ctypes.c_size_t()
+    _check(load().lsp_workspace_size(grid.handle, ctypes.byref(opts), ctypes.byref(b)))
+    return int(b.value)
+
+
+def lsp_cfl_dt(grid: Grid, opts: lsp_solve_opts, t: float, t_final: float) -> float:
+    dt = ctypes.c_double()
+    _check(load().lsp_cfl_dt(grid.handle, ctypes.byref(opts), t, t_final, ctypes.byref(dt)))
+    return dt.value
+
+
+def lsp_hj_rate(grid: Grid, opts, phi, rate, workspace, stream=None):
+    _check(load().lsp_hj_rate(grid.handle, ctypes.byref(opts), _ptr(phi), _ptr(rate),
+                              _ptr(workspace), _nbytes(workspace), _stream(stream)))
+
+
+def lsp_hj_step(grid: Grid, opts, phi, target, t, dt, workspace, stream=None) -> float:
+    d = ctypes.c_double(dt)
+    _check(load().lsp_hj_step(grid.handle, ctypes.byref(opts), _ptr(phi), _ptr(target), t,
+                              ctypes.byref(d), _ptr(workspace), _nbytes(workspace),
+                              _stream(stream)))
+    return d.value
+
+
+def lsp_hj_solve(grid: Grid, opts, phi, target, t0, t_final, workspace, stream=None) -> dict:
+    st = lsp_solve_stats()
+    _check(load().lsp_hj_solve(grid.handle, ctypes.byref(opts), _ptr(phi), _ptr(target), t0,
+                               t_final, _ptr(workspace), _nbytes(workspace), ctypes.byref(st),
+                               _stream(stream)))
+    return {"steps": st.steps, "stages": st.stages, "dt_min": st.dt_min, "dt_max": st.dt_max,
+            "t_end": st.t_end}
+
+
+def lsp_check_status(workspace, stream=None):
+    _check(load().lsp_check_status(_ptr(workspace), _stream(stream)))
+
+
+# ----------------------------------------------------------------- helpers
+class Problem:
+    """Grid + dynamics + options built from a problem description dict (the
+    format of :mod:`workloads`), with a workspace tensor of the right size."""
+
+    def __init__(self, spec: dict, device="cuda", check_finite=False, use_graph=False):
+        import torch
+        self.spec = spec
+        d = spec["ndim"]
+        self.grid = lsp_grid_create(d, spec["lo"], spec["hi"], spec["n"],
+                                    ["periodic" if p else "extrapolate" for p in spec["periodic"]])
+        lsp_set_dynamics(self.grid, spec["dyn"], spec["params"])
+        self.opts = make_opts(spec.get("rk", 3), spec["scheme"], spec.get("dtype", "f32"),
+                              spec.get("tube", False), spec.get("cfl", 0.75), check_finite,
+                              use_graph)
+        self.torch_dtype = torch.float64 if spec.get("dtype", "f32") == "f64" else torch.float32
+        nbytes = lsp_workspace_size(self.grid, self.opts)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+    def tensor(self, arr, device="cuda"):
+        import torch
+        return torch.as_tensor(arr).to(device=device, dtype=self.torch_dtype).contiguous()
+
+    def solve(self, phi, target=None, t0=0.0, t_final=None, stream=None):
+        tf = self.spec["t_final"] if t_final is None else t_final
+        return lsp_hj_solve(self.grid, self.opts, phi, target, t0, tf, self.workspace, stream)
+
+    def step(self, phi, target=None, t=0.0, dt=0.0, stream=None):
+        return lsp_hj_step(self.grid, self.opts, phi, target, t, dt, self.workspace, stream)
+
+    def rate(self, phi, out, stream=None):
+        lsp_hj_rate(self.grid, self.opts, phi, out, self.workspace, stream)
+        return out
+
+    def alpha(self):
+        return lsp_get_alpha(self.grid, self.spec["ndim"])

@@ -1,0 +1,81 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the
+C ABI and the FP64 oracle on the same seeded inputs, and compare.
+
+Tolerances.  FP64 kernels: rounding only, so 1e-11 relative to the scale of
+the compared quantity.  FP32 kernels: every one-sided derivative is a
+combination (coefficients summing in magnitude to < 4 after the 1/dx) of
+differences of stencil values, each carrying a relative rounding of u = 2^-24
+of max|phi|, so |dp_k| <~ 8 u max|phi| / dx_k; the rate then moves by at
+most sum_k (|dH/dp_k| + alpha_k) |dp_k| <= sum_k 2 alpha_k |dp_k| plus u |L|.
+The tests allow 8 times that:
+    tol_rate = 8 * (16 u max|phi| sum_k alpha_k / dx_k + u max|L|).
+A stage adds dt times that plus the rounding of the combination.  Where an
+ENO stencil choice is within 1e-4 (relative) of a tie, the FP32 and FP64
+choices may differ; those nodes are compared separately (they must be few).
+"""
+import numpy as np
+import torch
+
+import oracle
+from paper_2411_03501_gb300 import binding as B
+
+U32 = 2.0 ** -24
+U64 = 2.0 ** -53
+
+
+def to_dev(arr, dtype):
+    t = torch.float64 if dtype == "f64" else torch.float32
+    return torch.as_tensor(np.ascontiguousarray(arr)).to("cuda", t).contiguous()
+
+
+def rounded(arr, dtype):
+    """The input as the GPU sees it, in float64."""
+    return np.asarray(arr, dtype=np.float32 if dtype == "f32" else np.float64).astype(np.float64)
+
+
+def gpu_rate(spec, phi):
+    P = B.Problem(spec, check_finite=True)
+    x = to_dev(phi, spec["dtype"])
+    out = torch.empty_like(x)
+    P.rate(x, out)
+    torch.cuda.synchronize()
+    return out.double().cpu().numpy(), P
+
+
+def tie_margin(spec, phi):
+    m = np.ones(spec["n"])
+    if spec["scheme"] in ("eno2", "eno3"):
+        for k in range(spec["ndim"]):
+            _, _, t = oracle.derivs(spec, phi, k, with_ties=True)
+            m = np.minimum(m, t)
+    return m
+
+
+def rate_tol(spec, phi, L, alpha):
+    dx = oracle.dx(spec)
+    M = np.abs(phi).max()
+    if spec["dtype"] == "f64":
+        return 1e-11 * (M * float(np.sum(np.asarray(alpha) / dx)) + np.abs(L).max() + 1e-30)
+    return 8.0 * (16 * U32 * M * float(np.sum(np.asarray(alpha) / dx)) + U32 * np.abs(L).max())
+
+
+def compare(got, want, tol, ties=None, max_tie_frac=0.02, tie_bound=None):
+    """Element-wise |got - want| <= tol, except nodes near an ENO tie, which
+    must be rare (at most max_tie_frac) and within tie_bound (default: half
+    the largest |want| plus tol -- a flipped choice between candidates of
+    opposite sign moves the derivative by up to twice their magnitude)."""
+    err = np.abs(got - want)
+    if ties is None:
+        assert np.isfinite(got).all()
+        assert err.max() <= tol, f"max err {err.max():.3e} > tol {tol:.3e} at {np.unravel_index(err.argmax(), err.shape)}"
+        return err.max()
+    near = ties < 1e-4
+    assert near.mean() <= max_tie_frac, f"{near.mean():.3%} of nodes near an ENO tie"
+    far = ~near
+    if far.any():
+        e = err[far].max()
+        assert e <= tol, f"max err {e:.3e} > tol {tol:.3e} away from ties"
+    if near.any():
+        bound = tie_bound if tie_bound is not None else 0.5 * np.abs(want).max() + tol
+        assert np.isfinite(got[near]).all() and err[near].max() <= bound
+    return err[far].max() if far.any() else 0.0

@@ -1,0 +1,243 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element,
+on the same seeded inputs: every dimension x scheme x dynamics x precision
+on tiny grids (brute force), RK steps with the tube, whole solves of the
+workloads at reduced size, and single steps at full size."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_helpers import U32, compare, gpu_rate, rate_tol, rounded, tie_margin, to_dev
+from paper_2411_03501_gb300 import binding as B
+from paper_2411_03501_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SCHEMES = ["upwind1", "eno2", "eno3", "weno5"]
+SHAPES = {1: [23], 2: [16, 13], 3: [9, 8, 10], 4: [7, 8, 7, 9]}
+
+
+def _generic_spec(ndim, scheme, dyn, dtype):
+    lo = [-1.0, -0.5, 0.0, -2.0][:ndim]
+    hi = [1.0, 1.5, 2 * np.pi, 1.0][:ndim]
+    per = [False, True, True, False][:ndim]
+    params = {"normal_speed": [1.3], "translate": [0.7, -1.1, 0.4, 0.9][:ndim], "quadratic": []}[dyn]
+    return W.problem(ndim, SHAPES[ndim], lo, hi, per, scheme, dyn, params, dtype=dtype)
+
+
+def _cases():
+    out = []
+    for dtype in ("f32", "f64"):
+        for scheme in SCHEMES:
+            for ndim in (1, 2, 3, 4):
+                for dyn in ("normal_speed", "translate", "quadratic"):
+                    out.append(("generic", ndim, scheme, dyn, dtype))
+            out.append(("air3d", 3, scheme, "air3d", dtype))
+            out.append(("car4d", 4, scheme, "car4d", dtype))
+    return out
+
+
+def _spec_for(kind, ndim, scheme, dyn, dtype):
+    if kind == "air3d":
+        return W.air3d(nx=[9, 10, 11], scheme=scheme, dtype=dtype)[0]
+    if kind == "car4d":
+        spec = W.car4d(n=7, scheme=scheme, dtype=dtype)[0]
+        spec["n"] = [8, 7, 9, 7]
+        return spec
+    return _generic_spec(ndim, scheme, dyn, dtype)
+
+
+@pytest.mark.parametrize("kind,ndim,scheme,dyn,dtype", _cases())
+def test_rate_parity_brute_force(kind, ndim, scheme, dyn, dtype):
+    """L(phi) = -Hhat at every node of a tiny grid (Sec. IV-D), smooth plus
+    rough seeded data, against the oracle."""
+    spec = _spec_for(kind, ndim, scheme, dyn, dtype)
+    phi = W.smooth_field(spec, seed=ndim * 10 + len(dyn)) + 0.2 * W.rough_field(spec, seed=3)
+    phi = rounded(phi, dtype)
+    got, P = gpu_rate(spec, phi)
+    want, alpha = oracle.rate(spec, phi)
+    if dyn != "quadratic":
+        np.testing.assert_allclose(P.alpha(), alpha, rtol=1e-12, atol=1e-300)
+    tol = rate_tol(spec, phi, want, alpha)
+    ties = tie_margin(spec, phi) if dtype == "f32" else None
+    compare(got, want, tol, ties)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("rk", [1, 2, 3])
+@pytest.mark.parametrize("tube", [False, True])
+def test_rk_step_parity(dtype, rk, tube):
+    """One TVD-RK step (Sec. V-A) with an explicit dt, with and without the
+    min with the target (Sec. VI-A), on a ragged 3-D air3d grid."""
+    spec, phi0, g = W.air3d(nx=[19, 17, 21], scheme="weno5", rk=rk, dtype=dtype)
+    spec["tube"] = tube
+    phi0 = rounded(phi0 + 0.3 * W.smooth_field(spec, seed=5), dtype)
+    g = rounded(g, dtype)
+    a = oracle.alpha(spec, phi0)
+    dt = oracle.cfl_dt(spec, a, 0.75, 0.0, 10.0)
+    want = oracle.step(spec, phi0, dt, rk, target=g if tube else None)
+    P = B.Problem(spec, check_finite=True)
+    x = to_dev(phi0, dtype)
+    gt = to_dev(g, dtype)
+    used = P.step(x, gt if tube else None, t=0.0, dt=dt)
+    assert used == dt
+    got = x.double().cpu().numpy()
+    L, _ = oracle.rate(spec, phi0)
+    tol = rk * dt * rate_tol(spec, phi0, L, a) + (8 * U32 if dtype == "f32" else 1e-14) * np.abs(phi0).max()
+    compare(got, want, tol)
+    if tube:
+        assert np.all(got <= g)
+
+
+def test_config1_fp64_solve_matches_oracle_and_closed_form():
+    """The 2-D unit-speed front (101^2, ENO2, RK2, FP64): same 56 steps as
+    the oracle, same field to rounding, zero level set at radius 0.8."""
+    spec, phi0, _ = W.normal_speed_2d(101)
+    want, st_o = oracle.solve(spec, phi0, 0.5, 2, 0.9)
+    P = B.Problem(spec, check_finite=True)
+    x = to_dev(phi0, "f64")
+    st = P.solve(x, None, 0.0, 0.5)
+    got = x.cpu().numpy()
+    assert st["steps"] == st_o["steps"] == 56
+    assert st["t_end"] == pytest.approx(0.5, abs=1e-12)
+    err = np.abs(got - want).max()
+    assert err < 1e-9, err
+    n = spec["n"][0]
+    mid = n // 2
+    line = got[mid:, mid]
+    xx = W.axis_nodes(spec, 0)[mid:]
+    j = np.where(line > 0)[0][0]
+    rz = xx[j - 1] - line[j - 1] * (xx[j] - xx[j - 1]) / (line[j] - line[j - 1])
+    assert abs(rz - 0.8) < 0.5 * 0.02
+
+
+def _sign_ok(got, want, spec):
+    """Sign disagreements only at nodes next to the oracle's zero level set
+    (an axis neighbour of the node has the other oracle sign)."""
+    s = want > 0
+    near = np.zeros_like(s)
+    for k in range(spec["ndim"]):
+        for sh in (1, -1):
+            nb = np.roll(s, sh, axis=k)
+            near |= nb != s
+    bad = ((got > 0) != s) & ~near
+    return not bad.any(), int(((got > 0) != s).sum())
+
+
+@pytest.mark.slow
+def test_air3d_reduced_solve_fp32_within_tolerance():
+    """The air3d reachable tube (WENO5, RK3, tube) at 41^3 to t_final 2.8 in
+    FP32 against the FP64 oracle: max|dphi| <= 1e-4 max|phi|, signs differ
+    only within one cell of the interface."""
+    spec, phi0, g = W.air3d(n=41)
+    phi0 = rounded(phi0, "f32")
+    g32 = rounded(g, "f32")
+    want, st_o = oracle.solve(spec, phi0, 2.8, 3, 0.75, target=g32)
+    P = B.Problem(spec, check_finite=True)
+    x = to_dev(phi0, "f32")
+    st = P.solve(x, to_dev(g32, "f32"), 0.0, 2.8)
+    got = x.double().cpu().numpy()
+    assert st["steps"] == st_o["steps"]
+    assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
+    ok, nbad = _sign_ok(got, want, spec)
+    assert ok
+
+
+@pytest.mark.slow
+def test_car4d_reduced_solve_fp32_within_tolerance():
+    """The car4d tube (ENO3, RK3) at 17^4 to t_final 1.0 in FP32 against the
+    oracle, same bars as above."""
+    spec, phi0, g = W.car4d(n=17)
+    phi0 = rounded(phi0, "f32")
+    g32 = rounded(g, "f32")
+    want, st_o = oracle.solve(spec, phi0, 1.0, 3, 0.75, target=g32)
+    P = B.Problem(spec, check_finite=True)
+    x = to_dev(phi0, "f32")
+    st = P.solve(x, to_dev(g32, "f32"), 0.0, 1.0)
+    got = x.double().cpu().numpy()
+    assert st["steps"] == st_o["steps"]
+    assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
+    ok, _ = _sign_ok(got, want, spec)
+    assert ok
+
+
+def test_quadratic_solve_parity_device_alpha():
+    """H = |p|^2/2: the LF coefficients and the step come from a device
+    reduction over the current costate range every stage."""
+    spec = W.problem(2, [33, 29], [-1, -1], [1, 1], [False, False], "eno2", "quadratic", [],
+                     rk=2, cfl=0.5, t_final=0.3, dtype="f64")
+    xs = W.mesh(spec)
+    phi0 = np.sqrt(xs[0] ** 2 + xs[1] ** 2) - 0.5
+    want, st_o = oracle.solve(spec, phi0, 0.3, 2, 0.5)
+    P = B.Problem(spec, check_finite=True)
+    x = to_dev(phi0, "f64")
+    st = P.solve(x, None, 0.0, 0.3)
+    assert st["steps"] == st_o["steps"]
+    assert np.abs(x.cpu().numpy() - want).max() < 1e-9
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("which", ["air3d_201", "car4d_81"])
+def test_full_size_step_parity(which):
+    """One RK3 step of the full-size workloads (201^3 WENO5, 81^4 ENO3) in
+    the launch configuration the benchmark uses, element by element against
+    the oracle's step from the same FP32 input."""
+    if which == "air3d_201":
+        spec, phi0, g = W.air3d(n=201)
+    else:
+        spec, phi0, g = W.car4d(n=81)
+    phi0 = rounded(phi0, "f32")
+    g = rounded(g, "f32")
+    a = oracle.alpha(spec, phi0)
+    dt = oracle.cfl_dt(spec, a, 0.75, 0.0, spec["t_final"])
+    want = oracle.step(spec, phi0, dt, 3, target=g)
+    P = B.Problem(spec, check_finite=True)
+    np.testing.assert_allclose(P.alpha(), a, rtol=1e-12)
+    x = to_dev(phi0, "f32")
+    P.step(x, to_dev(g, "f32"), t=0.0, dt=dt)
+    got = x.double().cpu().numpy()
+    L, _ = oracle.rate(spec, phi0)
+    tol = 3 * dt * rate_tol(spec, phi0, L, a) + 8 * U32 * np.abs(phi0).max()
+    ties = tie_margin(spec, phi0) if spec["scheme"] in ("eno2", "eno3") else None
+    compare(got, want, tol, ties)
+
+
+def test_graph_replay_is_bitwise_identical():
+    """A solve replayed from a captured CUDA graph gives the same bits as
+    the eagerly launched one."""
+    spec, phi0, g = W.air3d(n=25, t_final=0.3)
+    P1 = B.Problem(spec)
+    P2 = B.Problem(spec, use_graph=True)
+    a = to_dev(phi0, "f32")
+    gt = to_dev(g, "f32")
+    s1 = P1.solve(a, gt)
+    for _ in range(2):  # capture, then replay
+        b = to_dev(phi0, "f32")
+        s2 = P2.solve(b, gt)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+        assert s1 == s2
+
+
+def test_nonfinite_is_reported():
+    spec, phi0, g = W.air3d(n=15, t_final=0.1)
+    P = B.Problem(spec, check_finite=True)
+    phi0 = phi0.copy()
+    phi0[7, 7, 7] = np.nan
+    x = to_dev(phi0, "f32")
+    with pytest.raises(B.LspError) as e:
+        P.step(x, to_dev(g, "f32"), t=0.0, dt=1e-3)
+    assert e.value.status == B.LSP_ENONFINITE
+
+
+def test_workspace_too_small_and_misaligned():
+    spec, phi0, g = W.air3d(n=15, t_final=0.1)
+    P = B.Problem(spec)
+    x = to_dev(phi0, "f32")
+    small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.LspError) as e:
+        B.lsp_hj_step(P.grid, P.opts, x, to_dev(g, "f32"), 0.0, 1e-3, small)
+    assert e.value.status == B.LSP_ENOMEM
+    with pytest.raises(B.LspError) as e:
+        B.lsp_hj_step(P.grid, P.opts, x.view(-1)[1:], to_dev(g, "f32"), 0.0, 1e-3, P.workspace)
+    assert e.value.status == B.LSP_EINVAL
