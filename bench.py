@@ -198,6 +198,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     P = B.Problem(spec, use_graph=args.graph)
     tdt = P.torch_dtype
     phi0_d = torch.as_tensor(phi0).to("cuda", tdt).contiguous()
+    tile = P.autotune(phi0_d) if args.autotune else P.tile()
     g_d = torch.as_tensor(g).to("cuda", tdt).contiguous() if g is not None else None
     phi = torch.empty_like(phi0_d)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -259,6 +260,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if args.graph:
         # the graph was captured for g_d; the e2e leg uses its own target buffer
         P_e2e = B.Problem(spec, use_graph=True)
+        if tile[0] > 0:
+            P_e2e.set_tile(*tile)
 
         def e2e_step():  # noqa: F811
             phi.copy_(h_phi0, non_blocking=True)
@@ -325,7 +328,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "config": {"workload": spec["name"], "points": npts, "stages_per_step": stages,
                    "rk_steps_per_step": stats["steps"], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed (512 MB write) between timed solves",
-                   "graph": bool(args.graph)},
+                   "graph": bool(args.graph), "tile": list(tile)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo},
         "gpu_launches": stages * args.steps,
@@ -334,6 +337,167 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batched(args, rank: int, world: int, local_rank: int):
+    """The batched workload: 256 problems (half 2-D normal speed, half 3-D
+    air3d, seeded sizes/speeds/radii) in one batched solve per benchmark
+    step; ranks split the problems round-robin by cost (no exchange).  The
+    single-problem path (one lsp_hj_solve per problem, in turn) is timed
+    beside it on the same problems."""
+    import numpy as np
+    import torch
+
+    from paper_2411_03501_gb300 import binding as B
+    from paper_2411_03501_gb300 import build as BLD
+    from paper_2411_03501_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0 or not os.path.exists(BLD.LIB):
+        BLD.build()
+    if world > 1:
+        torch.distributed.barrier()
+    allp = W.batched(256)
+    cost = [int(np.prod(sp["n"])) * (1 + i) for i, (sp, _, _) in enumerate(allp)]
+    order = sorted(range(len(allp)), key=lambda i: -cost[i])
+    mine = [allp[i] for k, i in enumerate(order) if k % world == rank]
+    specs = [m[0] for m in mine]
+    Bt = B.Batch(specs, use_graph=True)
+    h_phi0 = [torch.as_tensor(m[1], dtype=torch.float32).pin_memory() for m in mine]
+    h_g = [torch.as_tensor(m[2], dtype=torch.float32).pin_memory() for m in mine]
+    d_phi0 = [t.cuda() for t in h_phi0]
+    d_g = [t.cuda() for t in h_g]
+    phis = [torch.empty_like(t) for t in d_phi0]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def reset():
+        for a, b in zip(phis, d_phi0):
+            a.copy_(b)
+
+    for _ in range(args.warmup):
+        reset()
+        stats = Bt.solve(phis, d_g)
+    torch.cuda.synchronize()
+    units_rank = sum(int(np.prod(sp["n"])) * st["stages"] for sp, st in zip(specs, stats))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clk = ClockSampler(local_rank, os.path.join(args.outdir, f"clocks_rank{rank}.csv"))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with clk:
+        for i in range(args.steps):
+            reset()
+            flush.zero_()
+            ev[i][0].record(stream)
+            Bt.solve(phis, d_g)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    t = torch.tensor([ms, float(units_rank)], dtype=torch.float64, device="cuda")
+    tu = t.clone()
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tu, op=torch.distributed.ReduceOp.SUM)
+    ms = float(t[0].item())
+    units = float(tu[1].item()) * args.steps
+    value = units / (ms / 1e3)
+
+    # end to end: pinned host fields in, batched solve, fields out
+    h_out = [torch.empty_like(x).pin_memory() for x in h_phi0]
+    d_g2 = [torch.empty_like(x) for x in d_g]
+
+    def e2e():
+        for a, b in zip(phis, h_phi0):
+            a.copy_(b, non_blocking=True)
+        for a, b in zip(d_g2, h_g):
+            a.copy_(b, non_blocking=True)
+        Bt.solve(phis, d_g2)
+        for a, b in zip(h_out, phis):
+            a.copy_(b, non_blocking=True)
+
+    e2e()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t2 = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t2, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = units / (float(t2.item()) / 1e3)
+    bi = sum(x.numel() * 4 for x in h_phi0) + sum(x.numel() * 4 for x in h_g)
+    bo = sum(x.numel() * 4 for x in h_out)
+
+    # the single-problem path on the same problems, one solve after another
+    singles = [B.Problem(sp) for sp in specs]
+    reset()
+    for P, a, g in zip(singles, phis, d_g):  # warm-up
+        P.solve(a, g)
+    reset()
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for P, a, g in zip(singles, phis, d_g):
+        P.solve(a, g)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    single_value = float(units_rank) / (s0.elapsed_time(s1) / 1e3)
+    if rank != 0:
+        return 0
+    launches = max(st["steps"] for st in stats) * specs[0]["rk"]  # one launch per stage
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "batched_256_weno5_rk3_f32", "problems": len(allp),
+                   "points": sum(int(np.prod(p[0]["n"])) for p in allp),
+                   "parallelism": "problems split across ranks" if world > 1 else "single",
+                   "l2": "flushed (512 MB write) between timed solves", "graph": True,
+                   "single_problem_path_value": single_value},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
+                "d2h_bytes_per_step": bo},
+        "gpu_launches": launches * args.steps,
+        "roofline": None, "cpu_baseline": None, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_steps(args):
+    """Profiling mode: `warmup` then `steps` single RK steps of the workload
+    (3 stage launches each for RK3), timed with events; for ncu captures."""
+    import numpy as np
+    import torch
+
+    from paper_2411_03501_gb300 import binding as B
+    from paper_2411_03501_gb300 import build as BLD
+    BLD.build()
+    spec, phi0, g = workload(args.workload)
+    P = B.Problem(spec)
+    phi = torch.as_tensor(phi0).to("cuda", P.torch_dtype).contiguous()
+    gd = torch.as_tensor(g).to("cuda", P.torch_dtype).contiguous() if g is not None else None
+    tile = P.autotune(phi) if args.autotune else P.tile()
+    dt = B.lsp_cfl_dt(P.grid, P.opts, 0.0, spec["t_final"])
+    for _ in range(args.warmup):
+        P.step(phi, gd, 0.0, dt)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        P.step(phi, gd, 0.0, dt)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    print(json.dumps({"mode": "steps", "workload": spec["name"], "rk_steps": args.steps,
+                      "tile": tile,
+                      "ms_per_stage": ms / (args.steps * spec["rk"]),
+                      "points": int(np.prod(spec["n"]))}), flush=True)
     return 0
 
 
@@ -347,7 +511,11 @@ def main():
     ap.add_argument("--graph", type=int, default=0)
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--outdir", default=os.path.join(ROOT, "gpurun_out"))
+    ap.add_argument("--mode", default="solve", choices=["solve", "steps"])
+    ap.add_argument("--autotune", type=int, default=1)
     args = ap.parse_args()
+    if args.mode == "steps":
+        return run_steps(args)
     if args.warmup < 3:
         args.warmup = 3
     os.makedirs(args.outdir, exist_ok=True)
@@ -361,6 +529,8 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     try:
+        if args.workload == "batched":
+            return run_batched(args, rank, world, local_rank)
         return run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:

@@ -92,8 +92,12 @@ typedef struct {
                           produced                                         */
     int use_graph;     /* 1: lsp_hj_solve replays its launches as a CUDA
                           graph (captured on the first call with the same
-                          arguments, kept in the grid handle)              */
-    int reserved[6];   /* must be zero                                     */
+                          arguments, kept in the grid handle);
+                          lsp_hj_solve_batched captures its launches into
+                          one graph and launches that                      */
+    int batch_chunk;   /* batched solves: planes per CTA along the march of
+                          3-D/4-D problems (0 = 32)                        */
+    int reserved[5];   /* must be zero                                     */
 } lsp_solve_opts;
 
 typedef struct {
@@ -178,6 +182,100 @@ lsp_status lsp_hj_step(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
 lsp_status lsp_hj_solve(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
                         const void* target, double t0, double t_final, void* workspace,
                         size_t workspace_bytes, lsp_solve_stats* stats, void* stream);
+
+/* Tile of the tiled stage kernel used for FP32 grids of 3 or 4 dimensions
+ * (the generic one-thread-per-node kernel serves every other case).  A CTA
+ * of tb x ta threads covers tb nodes of the fastest axis and ta of the
+ * second fastest and marches along the third over ch planes; each plane of
+ * the tile is staged in shared memory with a 3-cell halo.  minb (2, 3 or 4)
+ * selects the kernel variant compiled for that many CTAs per SM (register
+ * budget 128, 80 or 64 per thread).
+ *  lsp_set_tile(g, 0, 0, 0, 0)   default (32 x 8, chunked for >= 2 waves, 3)
+ *  lsp_set_tile(g, -1, 0, 0, 0)  always use the generic kernel
+ *  lsp_set_tile(g, tb, ta, ch, minb) explicit; LSP_EINVAL unless
+ *        tb*ta <= 256, the haloed tile fits 4 values per thread, the launch
+ *        has <= 65535 z-blocks and minb is 2, 3 or 4.
+ * lsp_get_tile reports the tile a step with `opts` would use (all -1 when
+ * the generic kernel runs). */
+lsp_status lsp_set_tile(lsp_grid* grid, int tb, int ta, int ch, int minb);
+lsp_status lsp_get_tile(const lsp_grid* grid, const lsp_solve_opts* opts, int* tb, int* ta,
+                        int* ch, int* minb);
+
+/* Autotuner: time the first RK stage (phi -> workspace; phi is not
+ * modified) for a set of tile shapes, chunk lengths and occupancy targets
+ * (7 x 7 x 3 candidates, 3 timed launches each) on this grid and
+ * keep the fastest in the grid handle (reported through tb/ta/ch/minb, which may
+ * be NULL).  Waits for the GPU.  For grids without a tiled kernel it
+ * selects the generic one (all -1).  LSP_EUNSUPPORTED for QUADRATIC. */
+lsp_status lsp_autotune(lsp_grid* grid, const lsp_solve_opts* opts, const void* phi,
+                        void* workspace, size_t workspace_bytes, void* stream, int* tb, int* ta,
+                        int* ch, int* minb);
+
+/* Batched solves: nprob independent problems (own grid, dynamics, CFL step
+ * and t_final each) advanced together, problem i from t = 0 to t_final[i].
+ * One kernel launch advances one RK stage of every problem that still has
+ * steps left; CTAs map to (problem, tile) through a table in the workspace,
+ * so problems of different sizes and dimensions share every launch.
+ *  grids    nprob grids with state-only LF bounds (NORMAL_SPEED, TRANSLATE
+ *           in 2-4 D, AIR3D, CAR4D)
+ *  opts     shared: FP32, RK2 or RK3, scheme, CFL, tube, use_graph,
+ *           batch_chunk
+ *  phis     nprob device fields (in/out), targets: nprob device fields
+ *           (read if opts->tube)
+ *  t_final  nprob final times (host)
+ *  stats    nprob entries (host, nullable)
+ * Workspace: lsp_batched_workspace_size bytes (control block, problem
+ * table, CTA table, two stage fields per problem).  Each problem's result
+ * equals the single-problem solve of the same grid to FP32 rounding. */
+lsp_status lsp_batched_workspace_size(int nprob, lsp_grid* const* grids,
+                                      const lsp_solve_opts* opts, size_t* bytes);
+lsp_status lsp_hj_solve_batched(int nprob, lsp_grid* const* grids, const lsp_solve_opts* opts,
+                                void* const* phis, const void* const* targets,
+                                const double* t_final, void* workspace, size_t workspace_bytes,
+                                lsp_solve_stats* stats, void* stream);
+
+/* Discrete adjoint of a solve with a FIXED number of steps nsteps (dt from
+ * the CFL condition of the state-only GLF coefficients, no shortened last
+ * step), with sqrt(N) checkpointing.  The reverse replays every stage with
+ * the forward's selections frozen -- ENO stencils, the argmax inside the
+ * WENO regulariser, the signs of the optimal inputs, the min with the
+ * target, the grid node attaining each GLF coefficient -- and differentiates
+ * the rest exactly (the WENO weights included).  Dynamics parameters act
+ * through H, through the GLF coefficients and through dt.
+ *
+ * lsp_adjoint_workspace_size: bytes for ncheck checkpoints (0: ceil(sqrt
+ *   nsteps)), a segment of ceil(nsteps/ncheck) recomputed states, the stage
+ *   fields, five adjoint fields and 7*ndim coefficient fields.
+ * lsp_hj_solve_ckpt: the forward solve (phi in place), storing checkpoints
+ *   in the workspace.  Asynchronous.
+ * lsp_hj_adjoint: the reverse sweep from the checkpoints left in the same
+ *   workspace by lsp_hj_solve_ckpt (same grid, dynamics, opts, nsteps,
+ *   ncheck, target).
+ *   lamT        dLoss/dphi(t_end), device field (in)
+ *   lam0        dLoss/dphi0, device field (out)
+ *   lam_target  dLoss/dtarget, device field (out, nullable; tube only)
+ *   dprm        dLoss/dparams, 8 host doubles (out; the lsp_set_dynamics
+ *               parameters in order, the rest zero)
+ *   Waits for the GPU (reads the parameter accumulators).
+ * Not for QUADRATIC (LSP_EUNSUPPORTED). */
+lsp_status lsp_adjoint_workspace_size(const lsp_grid* grid, const lsp_solve_opts* opts,
+                                      int nsteps, int ncheck, size_t* bytes);
+lsp_status lsp_hj_solve_ckpt(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
+                             const void* target, int nsteps, int ncheck, void* workspace,
+                             size_t workspace_bytes, void* stream);
+lsp_status lsp_hj_adjoint(lsp_grid* grid, const lsp_solve_opts* opts, const void* target,
+                          int nsteps, int ncheck, const void* lamT, void* lam0, void* lam_target,
+                          double* dprm, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Loss of the differentiation workload and its gradient:
+ *   value = sum_i H_eps(-phi_i) dV + sum_q phi(x_q),
+ *   H_eps(s) = 1 / (1 + exp(-s/eps)), eps = max_k dx_k, dV = prod_k dx_k,
+ * phi(x_q) by multilinear interpolation at nq query states (device, nq x ndim
+ * row-major, same dtype; periodic axes wrap, others clamp).  value_dev: one
+ * device double (overwritten); grad: device field (overwritten, nullable).
+ * Asynchronous. */
+lsp_status lsp_loss_tube(const lsp_grid* grid, int dtype, const void* phi, const void* queries,
+                         int nq, double* value_dev, void* grad, void* stream);
 
 /* Wait for `stream` and report a device-side failure flagged in the
  * workspace control block since the last call that reset it (every step

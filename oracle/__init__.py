@@ -110,6 +110,11 @@ def lib():
         L.orc_ham.restype = ctypes.c_double
         L.orc_partial_bound.argtypes = [P, dp, ctypes.c_int]
         L.orc_partial_bound.restype = ctypes.c_double
+        L.orc_solve_steps.argtypes = [P, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int64]
+        L.orc_solve_steps.restype = ctypes.c_int
+        L.orc_adjoint.argtypes = [P, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_int64, dp, dp,
+                                  dp, dp, dp]
+        L.orc_adjoint.restype = ctypes.c_int
         L.orc_threads.argtypes = []
         L.orc_threads.restype = ctypes.c_int
         _lib = L
@@ -250,6 +255,100 @@ def solve(spec: dict, phi0, t_final: float, rk_order: int, cfl: float, target=No
                            int(max_steps), ctypes.byref(st)), "solve")
     return out, {"steps": st.steps, "stages": st.stages, "dt_min": st.dt_min,
                  "dt_max": st.dt_max, "t_end": st.t_end}
+
+
+def solve_steps(spec: dict, phi0, nsteps: int, rk_order: int, cfl: float, target=None):
+    """Fixed number of steps with the CFL step of the state-only GLF bounds
+    (no shortened last step): the forward map the adjoint reverses."""
+    p = _problem(spec)
+    out = _f64(phi0).reshape(spec["n"]).copy()
+    g = None if target is None else _f64(target).reshape(spec["n"])
+    _check(lib().orc_solve_steps(ctypes.byref(p), _ptr(out), _ptr(g) if g is not None else None,
+                                 int(rk_order), float(cfl), int(nsteps)), "solve_steps")
+    return out
+
+
+def adjoint(spec: dict, phi0, nsteps: int, rk_order: int, cfl: float, lamT, target=None):
+    """Discrete adjoint of solve_steps.  Returns (dL/dphi0, dL/dtarget or
+    None, dL/dparams (8), phi_T) for dL/dphi_T = lamT."""
+    p = _problem(spec)
+    phi0 = _f64(phi0).reshape(spec["n"])
+    lamT = _f64(lamT).reshape(spec["n"])
+    g = None if target is None else _f64(target).reshape(spec["n"])
+    lam0 = np.empty_like(phi0)
+    lamg = np.empty_like(phi0) if g is not None else None
+    dprm = np.zeros(8)
+    phiT = np.empty_like(phi0)
+    _check(lib().orc_adjoint(ctypes.byref(p), _ptr(phi0), _ptr(g) if g is not None else None,
+                             int(rk_order), float(cfl), int(nsteps), _ptr(lamT), _ptr(lam0),
+                             _ptr(lamg) if lamg is not None else None, _ptr(dprm), _ptr(phiT)),
+           "adjoint")
+    return lam0, lamg, dprm, phiT
+
+
+# ---------------------------------------------------------------- losses
+# The scalar losses of the differentiation workload (they are not in the
+# paper; plain numpy, FP64): a smoothed volume of {phi <= 0} and the sum of
+# phi at query states by multilinear interpolation.
+def _interp_weights(spec: dict, q):
+    """For each query row, the 2^d (flat node index, weight) pairs of
+    multilinear interpolation; periodic axes wrap, others clamp."""
+    d = spec["ndim"]
+    h = dx(spec)
+    idx = []
+    frac = []
+    for k in range(d):
+        t = (q[:, k] - spec["lo"][k]) / h[k]
+        n = spec["n"][k]
+        if spec["periodic"][k]:
+            i0 = np.floor(t).astype(np.int64)
+            f = t - i0
+            i0 = np.mod(i0, n)
+            i1 = np.mod(i0 + 1, n)
+        else:
+            t = np.clip(t, 0.0, n - 1.0)
+            i0 = np.minimum(np.floor(t).astype(np.int64), n - 2)
+            f = t - i0
+            i1 = i0 + 1
+        idx.append((i0, i1))
+        frac.append(f)
+    out = []
+    for corner in range(2 ** d):
+        w = np.ones(len(q))
+        flat = np.zeros(len(q), dtype=np.int64)
+        for k in range(d):
+            b = (corner >> (d - 1 - k)) & 1
+            w = w * (frac[k] if b else 1.0 - frac[k])
+            flat = flat * spec["n"][k] + idx[k][b]
+        out.append((flat, w))
+    return out
+
+
+def loss(spec: dict, phi, queries):
+    """sum_i H_eps(-phi_i) dV + sum_q phi(x_q), H_eps(s) = 1/(1+exp(-s/eps)),
+    eps = max dx, dV = prod dx."""
+    h = dx(spec)
+    eps = float(h.max())
+    dV = float(np.prod(h))
+    f = _f64(phi).ravel()
+    vol = np.sum(1.0 / (1.0 + np.exp(f / eps))) * dV
+    val = 0.0
+    for flat, w in _interp_weights(spec, np.asarray(queries, dtype=np.float64)):
+        val += np.sum(w * f[flat])
+    return float(vol + val)
+
+
+def loss_grad(spec: dict, phi, queries):
+    """d loss / d phi (same shape as phi)."""
+    h = dx(spec)
+    eps = float(h.max())
+    dV = float(np.prod(h))
+    f = _f64(phi).ravel()
+    Hs = 1.0 / (1.0 + np.exp(f / eps))  # H_eps(-phi)
+    g = -Hs * (1.0 - Hs) / eps * dV
+    for flat, w in _interp_weights(spec, np.asarray(queries, dtype=np.float64)):
+        np.add.at(g, flat, w)
+    return g.reshape(spec["n"])
 
 
 if __name__ == "__main__":  # pragma: no cover - manual build entry

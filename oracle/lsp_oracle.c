@@ -168,10 +168,22 @@ static double D3h(const double* u, int64_t j, double dx) /* D3_{j+1/2} */
     return (D2(u, j + 1, dx) - D2(u, j, dx)) / (3.0 * dx);
 }
 
-static double rel_margin(double a, double b)
+/* How close a selection between candidates a and b is to a tie that
+ * matters.  When a and b have the same sign, |a| ~ |b| means a ~ b, and
+ * taking the other one changes the result only at the level of the rounding
+ * that flipped the choice: margin 1.  Likewise when both candidates, times
+ * `weight` (which turns them into a derivative correction), are below 1e-6
+ * of the derivative's scale: a flip there moves the derivative by less than
+ * any tolerance the comparisons use.  With opposite signs the choice flips
+ * the correction term: the margin is ||a| - |b|| / (|a| + |b|).
+ * (Diagnostic output only; it does not enter any computed value.) */
+static double rel_margin(double a, double b, double weight, double scale)
 {
     double s = fabs(a) + fabs(b);
     if (s == 0.0) return 1.0; /* both zero: either choice gives the same value */
+    if ((a >= 0.0) == (b >= 0.0)) return 1.0;
+    /* both candidates at the rounding level of the derivative: no matter */
+    if (s * weight <= 1e-6 * scale) return 1.0;
     return fabs(fabs(a) - fabs(b)) / s;
 }
 
@@ -202,12 +214,13 @@ static double eno_at(const double* u, int64_t i, int64_t k, double dx, int order
         c = b;
         kstar = k;
     }
-    double m = rel_margin(a, b);
+    double scale = fabs(q1) + (fabs(a) + fabs(b)) * dx;
+    double m = rel_margin(a, b, dx, scale);
     double r = q1 + c * (double)(2 * (i - k) - 1) * dx;
     if (order >= 3) {
         double e = D3h(u, kstar, dx), f = D3h(u, kstar + 1, dx);
         double cs = (fabs(e) <= fabs(f)) ? e : f;
-        double mm = rel_margin(e, f);
+        double mm = rel_margin(e, f, dx * dx, scale + (fabs(e) + fabs(f)) * dx * dx);
         if (mm < m) m = mm;
         double s = (double)(i - kstar);
         r += cs * (3.0 * s * s - 6.0 * s + 2.0) * dx * dx;
@@ -643,4 +656,515 @@ double orc_ham(const orc_problem* P, const double* x, const double* p)
 double orc_partial_bound(const orc_problem* P, const double* x, int k)
 {
     return partial_bound(P, x, k);
+}
+
+/* ======================================================================== */
+/* Discrete adjoint of a solve with a FIXED number of steps.                 */
+/*                                                                          */
+/* The forward map is the scheme above with dt = cfl / sum_k alpha_k/dx_k   */
+/* (no shortened last step).  Its reverse is written out by hand: every     */
+/* selection the forward makes -- ENO stencils, the argmax inside the WENO  */
+/* regulariser, the signs of the optimal inputs, the min with the target,   */
+/* the grid node attaining each GLF coefficient -- is frozen at the forward */
+/* value, and the derivative of the smooth remainder is taken exactly (the  */
+/* WENO weights included).  Parameters act through H, through the GLF       */
+/* coefficients (via their argmax node) and through dt.                     */
+/* ======================================================================== */
+
+/* d(weno5_combine)/dv_m at v (same formula as weno5_combine):
+ *   F = sum_k w_k phi_k,  w_k = a_k / sum a,  a_k = d_k / (s_k + eps)^2
+ *   dF/dv = sum_k w_k dphi_k/dv - sum_k b_k (ds_k/dv + deps/dv),
+ *   b_k = 2 w_k (phi_k - F) / (s_k + eps). */
+static void weno5_combine_grad(const double* v, double* gv)
+{
+    double v1 = v[0], v2 = v[1], v3 = v[2], v4 = v[3], v5 = v[4];
+    double phi[3] = {v1 / 3.0 - 7.0 * v2 / 6.0 + 11.0 * v3 / 6.0,
+                     -v2 / 6.0 + 5.0 * v3 / 6.0 + v4 / 3.0,
+                     v3 / 3.0 + 5.0 * v4 / 6.0 - v5 / 6.0};
+    static const double dphi[3][5] = {{1.0 / 3.0, -7.0 / 6.0, 11.0 / 6.0, 0.0, 0.0},
+                                      {0.0, -1.0 / 6.0, 5.0 / 6.0, 1.0 / 3.0, 0.0},
+                                      {0.0, 0.0, 1.0 / 3.0, 5.0 / 6.0, -1.0 / 6.0}};
+    double a[3] = {v1 - 2.0 * v2 + v3, v2 - 2.0 * v3 + v4, v3 - 2.0 * v4 + v5};
+    double b[3] = {v1 - 4.0 * v2 + 3.0 * v3, v2 - v4, 3.0 * v3 - 4.0 * v4 + v5};
+    static const double da[3][5] = {{1, -2, 1, 0, 0}, {0, 1, -2, 1, 0}, {0, 0, 1, -2, 1}};
+    static const double db[3][5] = {{1, -4, 3, 0, 0}, {0, 1, 0, -1, 0}, {0, 0, 3, -4, 1}};
+    double s[3];
+    for (int k = 0; k < 3; ++k) s[k] = 13.0 / 12.0 * a[k] * a[k] + 0.25 * b[k] * b[k];
+    int mstar = 0; /* argmax of v^2 (first one on ties), frozen */
+    for (int m = 1; m < 5; ++m)
+        if (v[m] * v[m] > v[mstar] * v[mstar]) mstar = m;
+    double eps = 1e-6 * v[mstar] * v[mstar] + 1e-99;
+    static const double d[3] = {0.1, 0.6, 0.3};
+    double al[3], sum = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        al[k] = d[k] / ((s[k] + eps) * (s[k] + eps));
+        sum += al[k];
+    }
+    double F = 0.0, w[3];
+    for (int k = 0; k < 3; ++k) {
+        w[k] = al[k] / sum;
+        F += w[k] * phi[k];
+    }
+    double bsum = 0.0, bk[3];
+    for (int k = 0; k < 3; ++k) {
+        bk[k] = 2.0 * w[k] * (phi[k] - F) / (s[k] + eps);
+        bsum += bk[k];
+    }
+    for (int m = 0; m < 5; ++m) {
+        double gm = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            double ds = 13.0 / 6.0 * a[k] * da[k][m] + 0.5 * b[k] * db[k][m];
+            gm += w[k] * dphi[k][m] - bk[k] * ds;
+        }
+        if (m == mstar) gm -= bsum * 2e-6 * v[mstar];
+        gv[m] = gm;
+    }
+}
+
+/* Coefficients of the ENO derivative at node i built on base index k, as a
+ * combination of the extended line values u[i-3..i+3] (c[o+3]); the same
+ * selections as eno_at. */
+static void eno_at_coeffs(const double* u, int64_t i, int64_t k, double dx, int order, double* c)
+{
+    for (int o = 0; o < 7; ++o) c[o] = 0.0;
+    /* Q1' = D1_{k+1/2} = (u[k+1] - u[k]) / dx */
+    c[(k + 1) - i + 3] += 1.0 / dx;
+    c[k - i + 3] -= 1.0 / dx;
+    double a = D2(u, k, dx), b = D2(u, k + 1, dx);
+    int64_t j, kstar;
+    if (fabs(a) <= fabs(b)) {
+        j = k;
+        kstar = k - 1;
+    } else {
+        j = k + 1;
+        kstar = k;
+    }
+    /* c (2(i-k) - 1) dx with c = D2_j = (u[j+1] - 2u[j] + u[j-1]) / (2 dx^2) */
+    double f2 = (double)(2 * (i - k) - 1) * dx / (2.0 * dx * dx);
+    c[(j + 1) - i + 3] += f2;
+    c[j - i + 3] -= 2.0 * f2;
+    c[(j - 1) - i + 3] += f2;
+    if (order >= 3) {
+        double e = D3h(u, kstar, dx), f = D3h(u, kstar + 1, dx);
+        int64_t jj = (fabs(e) <= fabs(f)) ? kstar : kstar + 1;
+        /* D3_{jj+1/2} = (u[jj+2] - 3u[jj+1] + 3u[jj] - u[jj-1]) / (6 dx^3) */
+        double ss = (double)(i - kstar);
+        double f3 = (3.0 * ss * ss - 6.0 * ss + 2.0) * dx * dx / (6.0 * dx * dx * dx);
+        c[(jj + 2) - i + 3] += f3;
+        c[(jj + 1) - i + 3] -= 3.0 * f3;
+        c[jj - i + 3] += 3.0 * f3;
+        c[(jj - 1) - i + 3] -= f3;
+    }
+}
+
+/* Gradients of p^- and p^+ at node i w.r.t. u[i-3..i+3] (extended line). */
+static void deriv_window_grad(int scheme, const double* u, int64_t i, double dx, double* gm,
+                              double* gp)
+{
+    for (int o = 0; o < 7; ++o) gm[o] = gp[o] = 0.0;
+    if (scheme == ORC_UPWIND1) {
+        gm[3] = 1.0 / dx;
+        gm[2] = -1.0 / dx;
+        gp[4] = 1.0 / dx;
+        gp[3] = -1.0 / dx;
+    } else if (scheme == ORC_ENO2 || scheme == ORC_ENO3) {
+        int order = scheme == ORC_ENO2 ? 2 : 3;
+        eno_at_coeffs(u, i, i - 1, dx, order, gm);
+        eno_at_coeffs(u, i, i, dx, order, gp);
+    } else {
+        double d[6], vm[5], vp[5], g5[5];
+        for (int m = 0; m < 6; ++m) d[m] = (u[i - 3 + m + 1] - u[i - 3 + m]) / dx;
+        for (int m = 0; m < 5; ++m) {
+            vm[m] = d[m];
+            vp[m] = d[5 - m];
+        }
+        /* d[m] = (u[i-2+m] - u[i-3+m]) / dx  ->  window offsets m-2 and m-3 */
+        weno5_combine_grad(vm, g5);
+        for (int m = 0; m < 5; ++m) {
+            gm[m + 1] += g5[m] / dx;
+            gm[m] -= g5[m] / dx;
+        }
+        weno5_combine_grad(vp, g5);
+        for (int m = 0; m < 5; ++m) {
+            int dm = 5 - m; /* vp[m] = d[5-m] */
+            gp[dm + 1] += g5[m] / dx;
+            gp[dm] -= g5[m] / dx;
+        }
+    }
+}
+
+/* dH/dp_k (frozen input selections, sgn(0) = +1) and dH/dprm_j at (x, p). */
+static double sgn1(double v) { return v >= 0.0 ? 1.0 : -1.0; }
+
+static void ham_grads(const orc_problem* P, const double* x, const double* p, double* hp,
+                      double* hprm)
+{
+    const double* c = P->prm;
+    int d = P->ndim;
+    for (int j = 0; j < 8; ++j) hprm[j] = 0.0;
+    switch (P->dyn) {
+    case ORC_DYN_NORMAL_SPEED: {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s += p[k] * p[k];
+        s = sqrt(s);
+        for (int k = 0; k < d; ++k) hp[k] = s > 0.0 ? c[0] * p[k] / s : 0.0;
+        hprm[0] = s;
+        break;
+    }
+    case ORC_DYN_TRANSLATE:
+        for (int k = 0; k < d; ++k) {
+            hp[k] = c[k];
+            hprm[k] = p[k];
+        }
+        break;
+    case ORC_DYN_AIR3D: {
+        double ve = c[0], vp = c[1], um = c[2], dm = c[3];
+        double X = x[0], Y = x[1], th = x[2];
+        double s1 = p[0] * Y - p[1] * X - p[2];
+        double g1 = sgn1(s1), g3 = sgn1(p[2]);
+        hp[0] = -((-ve + vp * cos(th)) + um * g1 * Y);
+        hp[1] = -(vp * sin(th) - um * g1 * X);
+        hp[2] = um * g1 + dm * g3;
+        hprm[0] = p[0];
+        hprm[1] = -(p[0] * cos(th) + p[1] * sin(th));
+        hprm[2] = -fabs(s1);
+        hprm[3] = fabs(p[2]);
+        break;
+    }
+    case ORC_DYN_CAR4D: {
+        double th = x[2], v = x[3];
+        hp[0] = -v * cos(th);
+        hp[1] = -v * sin(th);
+        hp[2] = c[0] * sgn1(p[2]);
+        hp[3] = c[1] * sgn1(p[3]);
+        hprm[0] = fabs(p[2]);
+        hprm[1] = fabs(p[3]);
+        break;
+    }
+    }
+}
+
+/* d alpha_k / d prm_j through the grid node attaining alpha_k (the first
+ * one in C order, as alpha_from finds it). */
+static void alpha_grads(const orc_problem* P, double* dalpha /* [4][8] */)
+{
+    int64_t N = orc_npoints(P);
+    int d = P->ndim;
+    double best[ORC_MAXD];
+    int64_t at[ORC_MAXD];
+    for (int k = 0; k < d; ++k) {
+        best[k] = -1.0;
+        at[k] = 0;
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        double x[ORC_MAXD];
+        node_coords(P, i, x);
+        for (int k = 0; k < d; ++k) {
+            double b = partial_bound(P, x, k);
+            if (b > best[k]) {
+                best[k] = b;
+                at[k] = i;
+            }
+        }
+    }
+    for (int j = 0; j < 4 * 8; ++j) dalpha[j] = 0.0;
+    const double* c = P->prm;
+    for (int k = 0; k < d; ++k) {
+        double x[ORC_MAXD];
+        node_coords(P, at[k], x);
+        double* g = dalpha + 8 * k;
+        switch (P->dyn) {
+        case ORC_DYN_NORMAL_SPEED: g[0] = 1.0; break;
+        case ORC_DYN_TRANSLATE: g[k] = sgn1(c[k]); break;
+        case ORC_DYN_AIR3D:
+            if (k == 0) {
+                double w = -c[0] + c[1] * cos(x[2]);
+                g[0] = -sgn1(w);
+                g[1] = sgn1(w) * cos(x[2]);
+                g[2] = fabs(x[1]);
+            } else if (k == 1) {
+                g[1] = fabs(sin(x[2]));
+                g[2] = fabs(x[0]);
+            } else {
+                g[2] = 1.0;
+                g[3] = 1.0;
+            }
+            break;
+        case ORC_DYN_CAR4D:
+            if (k == 2) g[0] = 1.0;
+            if (k == 3) g[1] = 1.0;
+            break;
+        }
+    }
+}
+
+/* Node index of extended-line position e on a line (base, stride s, n
+ * nodes) and its weight, for ghost positions expressed through real nodes:
+ * up to two (node, weight) pairs. */
+static int ghost_terms(int64_t e, int64_t n, int periodic, int64_t* node, double* wt)
+{
+    if (e >= 0 && e < n) {
+        node[0] = e;
+        wt[0] = 1.0;
+        return 1;
+    }
+    if (periodic) {
+        node[0] = ((e % n) + n) % n;
+        wt[0] = 1.0;
+        return 1;
+    }
+    if (e < 0) { /* u0 + k (u0 - u1), k = -e */
+        double k = (double)(-e);
+        node[0] = 0;
+        wt[0] = 1.0 + k;
+        node[1] = 1;
+        wt[1] = -k;
+        return 2;
+    }
+    {
+        double k = (double)(e - (n - 1));
+        node[0] = n - 1;
+        wt[0] = 1.0 + k;
+        node[1] = n - 2;
+        wt[1] = -k;
+        return 2;
+    }
+}
+
+/* Reverse of one rate evaluation L(u) scaled by the per-node weights lam:
+ *   lam_u += J_L(u)^T lam,  hprm_acc += sum_i lam_i (-dH/dprm)(x_i, pbar_i),
+ *   alpha_acc[k] += sum_i lam_i (p+_k - p-_k)/2,  and returns sum_i lam_i L_i
+ * (the coefficient of dt). */
+static double rate_adjoint(const orc_problem* P, const double* u, const double* alpha,
+                           const double* lam, double* lam_u, double* hprm_acc, double* alpha_acc)
+{
+    int d = P->ndim;
+    int G = orc_ghost_width(P->scheme);
+    int64_t N = orc_npoints(P);
+    double* pm[ORC_MAXD];
+    double* pp[ORC_MAXD];
+    for (int k = 0; k < d; ++k) {
+        pm[k] = (double*)malloc(sizeof(double) * (size_t)N);
+        pp[k] = (double*)malloc(sizeof(double) * (size_t)N);
+        orc_derivs(P, u, k, pm[k], pp[k], NULL);
+    }
+    double dt_coef = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (lam[i] == 0.0) continue;
+        double x[ORC_MAXD], pbar[ORC_MAXD], hp[ORC_MAXD], hprm[8];
+        node_coords(P, i, x);
+        double diss = 0.0;
+        for (int k = 0; k < d; ++k) {
+            pbar[k] = 0.5 * (pp[k][i] + pm[k][i]);
+            diss += alpha[k] * 0.5 * (pp[k][i] - pm[k][i]);
+            alpha_acc[k] += lam[i] * 0.5 * (pp[k][i] - pm[k][i]);
+        }
+        dt_coef += lam[i] * (-(ham(P, x, pbar) - diss));
+        ham_grads(P, x, pbar, hp, hprm);
+        for (int j = 0; j < 8; ++j) hprm_acc[j] += lam[i] * (-hprm[j]);
+        /* scatter through every axis' window */
+        int64_t rem = i, coord[ORC_MAXD];
+        for (int k = d - 1; k >= 0; --k) {
+            coord[k] = rem % P->n[k];
+            rem /= P->n[k];
+        }
+        for (int k = 0; k < d; ++k) {
+            int64_t n = P->n[k], s = stride_of(P, k);
+            int64_t base = i - coord[k] * s; /* node 0 of this line */
+            /* extended line of this node's axis */
+            double* line = (double*)malloc(sizeof(double) * (size_t)n);
+            double* ext = (double*)malloc(sizeof(double) * (size_t)(n + 2 * G));
+            for (int64_t q = 0; q < n; ++q) line[q] = u[base + q * s];
+            fill_line(line, n, G, P->periodic[k], ext);
+            double gm[7], gp[7];
+            deriv_window_grad(P->scheme, ext + G, coord[k], orc_dx(P, k), gm, gp);
+            double sp = lam[i] * (-0.5 * hp[k] + 0.5 * alpha[k]);
+            double sm = lam[i] * (-0.5 * hp[k] - 0.5 * alpha[k]);
+            for (int o = -3; o <= 3; ++o) {
+                double c = sp * gp[o + 3] + sm * gm[o + 3];
+                if (c == 0.0) continue;
+                int64_t nodes[2];
+                double wts[2];
+                int cnt = ghost_terms(coord[k] + o, n, P->periodic[k], nodes, wts);
+                for (int q = 0; q < cnt; ++q) lam_u[base + nodes[q] * s] += c * wts[q];
+            }
+            free(line);
+            free(ext);
+        }
+    }
+    for (int k = 0; k < d; ++k) {
+        free(pm[k]);
+        free(pp[k]);
+    }
+    return dt_coef;
+}
+
+/* Forward solve with a fixed number of steps (dt from the CFL condition of
+ * the state-only GLF coefficients, no shortened last step). */
+int orc_solve_steps(const orc_problem* P, double* phi, const double* g, int rk_order, double cfl,
+                    int64_t nsteps)
+{
+    double alpha[ORC_MAXD];
+    int rc = orc_alpha(P, phi, alpha);
+    if (rc) return rc;
+    double dt = orc_cfl_dt(P, alpha, cfl, 0.0, INFINITY);
+    for (int64_t n = 0; n < nsteps && rc == 0; ++n) rc = orc_step(P, phi, g, rk_order, dt);
+    return rc;
+}
+
+/* Reverse sweep of orc_solve_steps (state-only GLF bounds).
+ *  lamT   dLoss/dphi(t_end)                                   (N, in)
+ *  lam0   dLoss/dphi0                                          (N, out)
+ *  lam_g  dLoss/dtarget (nullable; only with a target)         (N, out)
+ *  dprm   dLoss/dprm_j, j < 8, through H, alpha and dt          (out)
+ *  phiT   the forward end state (nullable)                     (N, out)
+ * Every forward stage input is stored, so memory is (steps * stages * N). */
+int orc_adjoint(const orc_problem* P, const double* phi0, const double* g, int rk, double cfl,
+                int64_t nsteps, const double* lamT, double* lam0, double* lam_g, double* dprm,
+                double* phiT)
+{
+    if (P->dyn == ORC_DYN_QUADRATIC) return -5;
+    int d = P->ndim;
+    int64_t N = orc_npoints(P);
+    double alpha[ORC_MAXD];
+    orc_alpha(P, phi0, alpha);
+    double S = 0.0;
+    for (int k = 0; k < d; ++k) S += alpha[k] / orc_dx(P, k);
+    double dt = cfl / S;
+    /* forward, storing the stage inputs u_0 = phi^n, u_1, u_2 */
+    size_t NS = (size_t)N;
+    double* st = (double*)malloc(sizeof(double) * NS * (size_t)(rk * nsteps + 1));
+    if (!st) return -4;
+    double* L = (double*)malloc(sizeof(double) * NS);
+    double* cur = (double*)malloc(sizeof(double) * NS);
+    memcpy(cur, phi0, sizeof(double) * NS);
+    for (int64_t n = 0; n < nsteps; ++n) {
+        double* u0 = st + NS * (size_t)(rk * n);
+        memcpy(u0, cur, sizeof(double) * NS);
+        orc_rate(P, u0, alpha, NULL, L);
+        if (rk == 1) {
+            for (size_t i = 0; i < NS; ++i) cur[i] = u0[i] + dt * L[i];
+        } else {
+            double* u1 = u0 + NS;
+            for (size_t i = 0; i < NS; ++i) u1[i] = u0[i] + dt * L[i];
+            orc_rate(P, u1, alpha, NULL, L);
+            if (rk == 2) {
+                for (size_t i = 0; i < NS; ++i) cur[i] = 0.5 * (u0[i] + u1[i] + dt * L[i]);
+            } else {
+                double* u2 = u1 + NS;
+                for (size_t i = 0; i < NS; ++i) u2[i] = 0.75 * u0[i] + 0.25 * (u1[i] + dt * L[i]);
+                orc_rate(P, u2, alpha, NULL, L);
+                for (size_t i = 0; i < NS; ++i)
+                    cur[i] = u0[i] / 3.0 + 2.0 / 3.0 * (u2[i] + dt * L[i]);
+            }
+        }
+        if (g)
+            for (size_t i = 0; i < NS; ++i)
+                if (g[i] < cur[i]) cur[i] = g[i];
+    }
+    if (phiT) memcpy(phiT, cur, sizeof(double) * NS);
+
+    /* reverse */
+    double* lam = (double*)malloc(sizeof(double) * NS);  /* dLoss/dphi^{n+1} */
+    double* ln = (double*)malloc(sizeof(double) * NS);   /* -> dLoss/dphi^n */
+    double* lv = (double*)malloc(sizeof(double) * NS);   /* before the min */
+    double* la = (double*)malloc(sizeof(double) * NS);   /* stage adjoints */
+    double* lb = (double*)malloc(sizeof(double) * NS);
+    double* w = (double*)malloc(sizeof(double) * NS);
+    memcpy(lam, lamT, sizeof(double) * NS);
+    if (lam_g) memset(lam_g, 0, sizeof(double) * NS);
+    double hprm_acc[8] = {0}, alpha_acc[ORC_MAXD] = {0, 0, 0, 0}, dt_acc = 0.0;
+    for (int64_t n = nsteps - 1; n >= 0; --n) {
+        double* u0 = st + NS * (size_t)(rk * n);
+        double* ulast = u0 + NS * (size_t)(rk - 1); /* input of the last stage */
+        /* value before the min: recompute the last stage */
+        orc_rate(P, ulast, alpha, NULL, L);
+        for (size_t i = 0; i < NS; ++i) {
+            double v;
+            if (rk == 1) v = u0[i] + dt * L[i];
+            else if (rk == 2) v = 0.5 * (u0[i] + ulast[i] + dt * L[i]);
+            else v = u0[i] / 3.0 + 2.0 / 3.0 * (ulast[i] + dt * L[i]);
+            if (g && g[i] < v) { /* the min took the target */
+                lv[i] = 0.0;
+                if (lam_g) lam_g[i] += lam[i];
+            } else {
+                lv[i] = lam[i];
+            }
+        }
+        memset(ln, 0, sizeof(double) * NS);
+        if (rk == 1) {
+            /* phi^{n+1} = u0 + dt L(u0) */
+            for (size_t i = 0; i < NS; ++i) {
+                ln[i] += lv[i];
+                w[i] = dt * lv[i];
+            }
+            dt_acc += rate_adjoint(P, u0, alpha, w, ln, hprm_acc, alpha_acc) / dt;
+        } else if (rk == 2) {
+            double* u1 = u0 + NS;
+            /* phi^{n+1} = 1/2 u0 + 1/2 u1 + 1/2 dt L(u1) */
+            memset(la, 0, sizeof(double) * NS);
+            for (size_t i = 0; i < NS; ++i) {
+                ln[i] += 0.5 * lv[i];
+                la[i] += 0.5 * lv[i];
+                w[i] = 0.5 * dt * lv[i];
+            }
+            dt_acc += rate_adjoint(P, u1, alpha, w, la, hprm_acc, alpha_acc) / dt;
+            /* u1 = u0 + dt L(u0) */
+            for (size_t i = 0; i < NS; ++i) {
+                ln[i] += la[i];
+                w[i] = dt * la[i];
+            }
+            dt_acc += rate_adjoint(P, u0, alpha, w, ln, hprm_acc, alpha_acc) / dt;
+        } else {
+            double* u1 = u0 + NS;
+            double* u2 = u1 + NS;
+            /* phi^{n+1} = 1/3 u0 + 2/3 u2 + 2/3 dt L(u2) */
+            memset(lb, 0, sizeof(double) * NS);
+            for (size_t i = 0; i < NS; ++i) {
+                ln[i] += lv[i] / 3.0;
+                lb[i] += 2.0 / 3.0 * lv[i];
+                w[i] = 2.0 / 3.0 * dt * lv[i];
+            }
+            dt_acc += rate_adjoint(P, u2, alpha, w, lb, hprm_acc, alpha_acc) / dt;
+            /* u2 = 3/4 u0 + 1/4 u1 + 1/4 dt L(u1) */
+            memset(la, 0, sizeof(double) * NS);
+            for (size_t i = 0; i < NS; ++i) {
+                ln[i] += 0.75 * lb[i];
+                la[i] += 0.25 * lb[i];
+                w[i] = 0.25 * dt * lb[i];
+            }
+            dt_acc += rate_adjoint(P, u1, alpha, w, la, hprm_acc, alpha_acc) / dt;
+            /* u1 = u0 + dt L(u0) */
+            for (size_t i = 0; i < NS; ++i) {
+                ln[i] += la[i];
+                w[i] = dt * la[i];
+            }
+            dt_acc += rate_adjoint(P, u0, alpha, w, ln, hprm_acc, alpha_acc) / dt;
+        }
+        memcpy(lam, ln, sizeof(double) * NS);
+    }
+    memcpy(lam0, lam, sizeof(double) * NS);
+    /* hprm_acc and alpha_acc were accumulated with weights c dt lam: they are
+     * already dLoss/dprm (direct) and dLoss/dalpha (dissipation).  dt_acc is
+     * dLoss/ddt.  dt = cfl / S(alpha):  ddt/dalpha_k = -cfl / (S^2 dx_k). */
+    double dal[4 * 8];
+    alpha_grads(P, dal);
+    for (int j = 0; j < 8; ++j) {
+        double v = hprm_acc[j];
+        for (int k = 0; k < d; ++k) {
+            double dL_dalpha = alpha_acc[k] - dt_acc * cfl / (S * S * orc_dx(P, k));
+            v += dL_dalpha * dal[8 * k + j];
+        }
+        dprm[j] = v;
+    }
+    free(st);
+    free(L);
+    free(cur);
+    free(lam);
+    free(ln);
+    free(lv);
+    free(la);
+    free(lb);
+    free(w);
+    return 0;
 }

@@ -1,0 +1,92 @@
+"""PyTorch autograd wrappers of the discrete adjoint (argument marshalling
+only: the forward solve, the reverse sweep and the loss run in the CUDA
+library).
+
+``HJTube(spec, nsteps)`` holds a grid and a workspace; ``tube(phi0, target,
+params)`` returns phi after ``nsteps`` fixed CFL steps and is differentiable
+with respect to phi0, the target and the dynamics parameters (the reverse
+sweep of ``lsp_hj_adjoint`` with sqrt(N) checkpoints).  ``tube.loss(phi,
+queries)`` is the smoothed tube volume plus the values at query states,
+differentiable with respect to phi.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import binding as B
+
+
+class _SolveFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, phi0, target, params, tube):
+        tube._set_params(params)
+        phi = phi0.detach().clone().contiguous()
+        tgt = target.detach().contiguous() if target is not None else None
+        B.lsp_hj_solve_ckpt(tube.grid, tube.opts, phi, tgt, tube.nsteps, tube.ncheck,
+                            tube.workspace)
+        ctx.tube = tube
+        ctx.params = params.detach().clone()
+        ctx.save_for_backward(tgt if tgt is not None else torch.empty(0))
+        ctx.has_target = tgt is not None
+        return phi
+
+    @staticmethod
+    def backward(ctx, grad_phi):
+        tube = ctx.tube
+        (tgt,) = ctx.saved_tensors
+        tgt = tgt if ctx.has_target else None
+        tube._set_params(ctx.params)  # the sweep needs the forward's dynamics
+        lamT = grad_phi.contiguous()
+        lam0 = torch.empty_like(lamT)
+        lamg = torch.empty_like(lamT) if tgt is not None else None
+        dprm = B.lsp_hj_adjoint(tube.grid, tube.opts, tgt, tube.nsteps, tube.ncheck, lamT, lam0,
+                                lamg, tube.workspace)
+        gp = torch.tensor(dprm[: ctx.params.numel()], dtype=ctx.params.dtype,
+                          device=ctx.params.device)
+        return lam0, lamg, gp, None
+
+
+class _LossFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, phi, queries, tube):
+        value = torch.zeros(1, dtype=torch.float64, device=phi.device)
+        grad = torch.empty_like(phi)
+        B.lsp_loss_tube(tube.grid, tube.spec.get("dtype", "f32"), phi.contiguous(),
+                        queries.contiguous() if queries is not None else None, value, grad)
+        ctx.save_for_backward(grad)
+        return value[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return grad * g.to(grad.dtype), None, None
+
+
+class HJTube:
+    """A fixed-step reachable-tube solve with a discrete-adjoint backward."""
+
+    def __init__(self, spec: dict, nsteps: int, ncheck: int = 0, device="cuda"):
+        self.spec = spec
+        self.nsteps = int(nsteps)
+        self.ncheck = int(ncheck)
+        d = spec["ndim"]
+        self.grid = B.lsp_grid_create(d, spec["lo"], spec["hi"], spec["n"],
+                                      ["periodic" if p else "extrapolate" for p in spec["periodic"]])
+        self._params = None
+        self._set_params(torch.tensor(spec["params"], dtype=torch.float64))
+        self.opts = B.make_opts(spec.get("rk", 3), spec["scheme"], spec.get("dtype", "f32"),
+                                spec.get("tube", False), spec.get("cfl", 0.75))
+        nbytes = B.lsp_adjoint_workspace_size(self.grid, self.opts, self.nsteps, self.ncheck)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+    def _set_params(self, params):
+        p = [float(v) for v in params.detach().cpu().reshape(-1)]
+        if p != self._params:
+            B.lsp_set_dynamics(self.grid, self.spec["dyn"], p)
+            self._params = p
+
+    def __call__(self, phi0, target, params):
+        return _SolveFn.apply(phi0, target, params, self)
+
+    def loss(self, phi, queries):
+        return _LossFn.apply(phi, queries, self)

@@ -25,6 +25,9 @@ EXPORTS = [
     "lsp_version", "lsp_status_string", "lsp_last_error", "lsp_grid_create", "lsp_grid_destroy",
     "lsp_set_dynamics", "lsp_get_alpha", "lsp_workspace_size", "lsp_cfl_dt", "lsp_hj_rate",
     "lsp_hj_step", "lsp_hj_solve", "lsp_check_status",
+    "lsp_set_tile", "lsp_get_tile", "lsp_autotune", "lsp_batched_workspace_size",
+    "lsp_hj_solve_batched", "lsp_adjoint_workspace_size", "lsp_hj_solve_ckpt", "lsp_hj_adjoint",
+    "lsp_loss_tube",
 ]
 
 
@@ -43,7 +46,8 @@ class lsp_solve_opts(ctypes.Structure):
         ("cfl", ctypes.c_double),
         ("check_finite", ctypes.c_int),
         ("use_graph", ctypes.c_int),
-        ("reserved", ctypes.c_int * 6),
+        ("batch_chunk", ctypes.c_int),
+        ("reserved", ctypes.c_int * 5),
     ]
 
 
@@ -90,6 +94,23 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.lsp_hj_solve.argtypes = [vp, op, vp, vp, ctypes.c_double, ctypes.c_double, vp, sz,
                                ctypes.POINTER(lsp_solve_stats), vp]
     L.lsp_check_status.argtypes = [vp, vp]
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.lsp_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.lsp_get_tile.argtypes = [vp, op, ip, ip, ip, ip]
+    L.lsp_autotune.argtypes = [vp, op, vp, vp, sz, vp, ip, ip, ip, ip]
+    pp = ctypes.POINTER(vp)
+    L.lsp_batched_workspace_size.argtypes = [ctypes.c_int, pp, op, ctypes.POINTER(sz)]
+    L.lsp_hj_solve_batched.argtypes = [ctypes.c_int, pp, op, pp, pp, dp, vp, sz,
+                                       ctypes.POINTER(lsp_solve_stats), vp]
+    ci = ctypes.c_int
+    L.lsp_adjoint_workspace_size.argtypes = [vp, op, ci, ci, ctypes.POINTER(sz)]
+    L.lsp_hj_solve_ckpt.argtypes = [vp, op, vp, vp, ci, ci, vp, sz, vp]
+    L.lsp_hj_adjoint.argtypes = [vp, op, vp, ci, ci, vp, vp, vp, dp, vp, sz, vp]
+    L.lsp_loss_tube.argtypes = [vp, ci, vp, vp, ci, vp, vp, vp]
+    for name in ("lsp_set_tile", "lsp_get_tile", "lsp_autotune", "lsp_batched_workspace_size",
+                 "lsp_hj_solve_batched", "lsp_adjoint_workspace_size", "lsp_hj_solve_ckpt",
+                 "lsp_hj_adjoint", "lsp_loss_tube"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("lsp_grid_create", "lsp_set_dynamics", "lsp_get_alpha", "lsp_workspace_size",
                  "lsp_cfl_dt", "lsp_hj_rate", "lsp_hj_step", "lsp_hj_solve", "lsp_check_status"):
         getattr(L, name).restype = ctypes.c_int
@@ -202,6 +223,105 @@ def lsp_hj_solve(grid: Grid, opts, phi, target, t0, t_final, workspace, stream=N
             "t_end": st.t_end}
 
 
+def lsp_set_tile(grid: Grid, tb: int, ta: int, ch: int, minb: int = 3):
+    _check(load().lsp_set_tile(grid.handle, tb, ta, ch, minb))
+
+
+def lsp_get_tile(grid: Grid, opts) -> tuple:
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(load().lsp_get_tile(grid.handle, ctypes.byref(opts), *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def lsp_autotune(grid: Grid, opts, phi, workspace, stream=None) -> tuple:
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(load().lsp_autotune(grid.handle, ctypes.byref(opts), _ptr(phi), _ptr(workspace),
+                               _nbytes(workspace), _stream(stream),
+                               *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def _handles(grids):
+    arr = (ctypes.c_void_p * len(grids))()
+    for i, g in enumerate(grids):
+        arr[i] = g.handle.value
+    return arr
+
+
+def lsp_batched_workspace_size(grids, opts) -> int:
+    b = ctypes.c_size_t()
+    _check(load().lsp_batched_workspace_size(len(grids), _handles(grids), ctypes.byref(opts),
+                                             ctypes.byref(b)))
+    return int(b.value)
+
+
+def lsp_hj_solve_batched(grids, opts, phis, targets, t_final, workspace, stream=None) -> list:
+    n = len(grids)
+    P = (ctypes.c_void_p * n)(*[t.data_ptr() for t in phis])
+    T = (ctypes.c_void_p * n)(*[t.data_ptr() for t in targets]) if targets is not None else None
+    tf = (ctypes.c_double * n)(*[float(v) for v in t_final])
+    st = (lsp_solve_stats * n)()
+    _check(load().lsp_hj_solve_batched(n, _handles(grids), ctypes.byref(opts), P, T, tf,
+                                       _ptr(workspace), _nbytes(workspace), st, _stream(stream)))
+    return [{"steps": s.steps, "stages": s.stages, "dt_min": s.dt_min, "dt_max": s.dt_max,
+             "t_end": s.t_end} for s in st]
+
+
+def lsp_adjoint_workspace_size(grid: Grid, opts, nsteps: int, ncheck: int = 0) -> int:
+    b = ctypes.c_size_t()
+    _check(load().lsp_adjoint_workspace_size(grid.handle, ctypes.byref(opts), int(nsteps),
+                                             int(ncheck), ctypes.byref(b)))
+    return int(b.value)
+
+
+def lsp_hj_solve_ckpt(grid: Grid, opts, phi, target, nsteps, ncheck, workspace, stream=None):
+    _check(load().lsp_hj_solve_ckpt(grid.handle, ctypes.byref(opts), _ptr(phi), _ptr(target),
+                                    int(nsteps), int(ncheck), _ptr(workspace),
+                                    _nbytes(workspace), _stream(stream)))
+
+
+def lsp_hj_adjoint(grid: Grid, opts, target, nsteps, ncheck, lamT, lam0, lam_target, workspace,
+                   stream=None) -> list:
+    d = (ctypes.c_double * 8)()
+    _check(load().lsp_hj_adjoint(grid.handle, ctypes.byref(opts), _ptr(target), int(nsteps),
+                                 int(ncheck), _ptr(lamT), _ptr(lam0), _ptr(lam_target), d,
+                                 _ptr(workspace), _nbytes(workspace), _stream(stream)))
+    return [d[i] for i in range(8)]
+
+
+def lsp_loss_tube(grid: Grid, dtype, phi, queries, value_dev, grad=None, stream=None):
+    dt = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    nq = 0 if queries is None else queries.shape[0]
+    _check(load().lsp_loss_tube(grid.handle, dt, _ptr(phi), _ptr(queries), nq, _ptr(value_dev),
+                                _ptr(grad), _stream(stream)))
+
+
+class Batch:
+    """Batched solve of several problem descriptions (dicts of
+    :mod:`workloads`) sharing scheme, RK order, CFL and tube."""
+
+    def __init__(self, specs, device="cuda", check_finite=False, use_graph=True, chunk=0):
+        import torch
+        self.specs = specs
+        self.grids = []
+        for sp in specs:
+            g = lsp_grid_create(sp["ndim"], sp["lo"], sp["hi"], sp["n"],
+                                ["periodic" if p else "extrapolate" for p in sp["periodic"]])
+            lsp_set_dynamics(g, sp["dyn"], sp["params"])
+            self.grids.append(g)
+        s0 = specs[0]
+        self.opts = make_opts(s0.get("rk", 3), s0["scheme"], "f32", s0.get("tube", False),
+                              s0.get("cfl", 0.75), check_finite, use_graph)
+        self.opts.batch_chunk = int(chunk)
+        nbytes = lsp_batched_workspace_size(self.grids, self.opts)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+    def solve(self, phis, targets=None, t_final=None, stream=None):
+        tf = [sp["t_final"] for sp in self.specs] if t_final is None else t_final
+        return lsp_hj_solve_batched(self.grids, self.opts, phis, targets, tf, self.workspace,
+                                    stream)
+
+
 def lsp_check_status(workspace, stream=None):
     _check(load().lsp_check_status(_ptr(workspace), _stream(stream)))
 
@@ -242,3 +362,12 @@ class Problem:
 
     def alpha(self):
         return lsp_get_alpha(self.grid, self.spec["ndim"])
+
+    def set_tile(self, tb, ta=0, ch=0, minb=3):
+        lsp_set_tile(self.grid, tb, ta, ch, minb)
+
+    def tile(self):
+        return lsp_get_tile(self.grid, self.opts)
+
+    def autotune(self, phi, stream=None):
+        return lsp_autotune(self.grid, self.opts, phi, self.workspace, stream)

@@ -1,0 +1,512 @@
+// adjoint.cuh -- reverse of one fused Runge-Kutta stage.
+//
+// Forward stage (stage_generic.cuh / stage_tiled.cuh):
+//   v   = c_n phi^n + c_s u + c_l dt L(u),   out = min(v, g) in a tube stage
+//   L_i = -H(x_i, pbar_i) + sum_k alpha_k (p+_k,i - p-_k,i) / 2
+// Given lam = dLoss/dout, the reverse gives dLoss/du, dLoss/dphi^n,
+// dLoss/dg and the sensitivities to the dynamics parameters, alpha and dt.
+// Every selection the forward made (ENO stencils, the argmax inside the WENO
+// regulariser, the signs of the optimal inputs, the min with the target) is
+// recomputed from the same stage input and frozen; the smooth remainder --
+// WENO weights included -- is differentiated exactly.
+//
+// Two kernels per stage.  adj_stage_a (one thread per node i) recomputes the
+// node's forward quantities, forms the weighted sensitivities of p+-_k,i and
+// stores, per axis, the 7 coefficients c_k,i[o] = dLoss/du at window offset
+// o; window positions that fall on ghost cells of an extrapolated axis are
+// folded onto their boundary nodes right away (atomics, boundary nodes only).
+// adj_stage_b (one thread per node j) gathers sum_k sum_o c_k,(j-o e_k)[o]
+// (periodic axes wrap) -- deterministic, no atomics on the interior.
+#pragma once
+#include "stage_generic.cuh"
+#include "stage_tiled.cuh"
+
+namespace lsp {
+
+// ---------------------------------------------------------------------------
+// Window gradients: gm[o], gp[o] = d p-/du[o], d p+/du[o], o = 0..6 for the
+// window offsets -3..3 (the stencils of G < 3 use the middle entries).
+
+template <typename R>
+__device__ __forceinline__ void grad_upwind1(R inv_dx, R* gm, R* gp)
+{
+    gm[2] += -inv_dx; gm[3] += inv_dx;
+    gp[3] += -inv_dx; gp[4] += inv_dx;
+}
+
+// ENO2/ENO3 on the window u[0..6] (offset -3..3): the same unscaled
+// differences and the same comparisons as deriv_eno2 / deriv_eno3, so the
+// frozen stencil is the forward's; the derivative is then a fixed linear
+// combination of window values.
+template <typename R>
+__device__ __forceinline__ void add_D(R* g, int m, R w)  // D_m = u_{m+1} - u_m
+{
+    g[m + 4] += w; g[m + 3] -= w;
+}
+template <typename R>
+__device__ __forceinline__ void add_S(R* g, int m, R w)  // S_m = u_{m+1} - 2u_m + u_{m-1}
+{
+    g[m + 4] += w; g[m + 3] -= R(2) * w; g[m + 2] += w;
+}
+template <typename R>
+__device__ __forceinline__ void add_T(R* g, int m, R w)  // T_m = S_{m+1} - S_m
+{
+    add_S(g, m + 1, w); add_S(g, m, -w);
+}
+
+template <typename R, int ORDER>
+__device__ __forceinline__ void grad_eno(const R* u7, R inv_dx, R* gm, R* gp)
+{
+    // unscaled differences at offsets, as in the forward kernels
+    const R dm3 = u7[1] - u7[0], dm2 = u7[2] - u7[1], dm1 = u7[3] - u7[2];
+    const R d0 = u7[4] - u7[3], d1 = u7[5] - u7[4], d2 = u7[6] - u7[5];
+    const R Sm2 = dm2 - dm3, Sm1 = dm1 - dm2, S0 = d0 - dm1, S1 = d1 - d0, S2 = d2 - d1;
+    const R Tm2 = Sm1 - Sm2, Tm1 = S0 - Sm1, T0 = S1 - S0, T1 = S2 - S1;
+    (void)Tm2; (void)T1;
+    // left: p- = (d_-1 + S_c / 2 [+ T_c f / 6]) / dx
+    add_D(gm, -1, inv_dx);
+    if (rabs(Sm1) <= rabs(S0)) {
+        add_S(gm, -1, R(0.5) * inv_dx);
+        if (ORDER == 3) {
+            if (rabs(Tm2) <= rabs(Tm1)) add_T(gm, -2, R(2.0 / 6.0) * inv_dx);
+            else add_T(gm, -1, R(2.0 / 6.0) * inv_dx);
+        }
+    } else {
+        add_S(gm, 0, R(0.5) * inv_dx);
+        if (ORDER == 3) {
+            if (rabs(Tm1) <= rabs(T0)) add_T(gm, -1, R(-1.0 / 6.0) * inv_dx);
+            else add_T(gm, 0, R(-1.0 / 6.0) * inv_dx);
+        }
+    }
+    // right: p+ = (d_0 - S_c / 2 [+ T_c f / 6]) / dx
+    add_D(gp, 0, inv_dx);
+    if (rabs(S0) <= rabs(S1)) {
+        add_S(gp, 0, R(-0.5) * inv_dx);
+        if (ORDER == 3) {
+            if (rabs(Tm1) <= rabs(T0)) add_T(gp, -1, R(-1.0 / 6.0) * inv_dx);
+            else add_T(gp, 0, R(-1.0 / 6.0) * inv_dx);
+        }
+    } else {
+        add_S(gp, 1, R(-0.5) * inv_dx);
+        if (ORDER == 3) {
+            if (rabs(T0) <= rabs(T1)) add_T(gp, 0, R(2.0 / 6.0) * inv_dx);
+            else add_T(gp, 1, R(2.0 / 6.0) * inv_dx);
+        }
+    }
+}
+
+// Gradient of the Jiang-Peng term Phi(a,b,c,d) (see deriv_weno5_jp) with
+// respect to a, b, c, d and to the regulariser e:
+//   Phi = w0 A + (w2 - 1/2) B,  A = (a - 2b + c)/3,  B = (b - 2c + d)/6,
+//   w_k = C_k/(IS_k + e)^2 / sum_l C_l/(IS_l + e)^2,  C = (1, 6, 3),
+//   dw_k = w_k (g_k - sum_l w_l g_l),  g_k = -2 (dIS_k + de)/(IS_k + e).
+template <typename R>
+__device__ __forceinline__ void weno_phi_grad(R a, R b, R c, R d, R e, R* gabcd, R* ge)
+{
+    const R f0 = a - R(3) * b, f1 = b + c, f2 = R(3) * c - d;
+    const R is0 = R(13) * (a - b) * (a - b) + R(3) * f0 * f0;
+    const R is1 = R(13) * (b - c) * (b - c) + R(3) * f1 * f1;
+    const R is2 = R(13) * (c - d) * (c - d) + R(3) * f2 * f2;
+    const R q0 = is0 + e, q1 = is1 + e, q2 = is2 + e;
+    // weights (the common scale of q cancels; 1/q^2 may be large, so form
+    // ratios to the largest weight)
+    const R r0 = R(1) / q0, r1 = R(1) / q1, r2 = R(1) / q2;
+    const R a0 = r0 * r0, a1 = R(6) * r1 * r1, a2 = R(3) * r2 * r2;
+    const R inv = R(1) / (a0 + a1 + a2);
+    const R w0 = a0 * inv, w1 = a1 * inv, w2 = a2 * inv;
+    const R A = (a - R(2) * b + c) * R(1.0 / 3.0), B = (b - R(2) * c + d) * R(1.0 / 6.0);
+    const R E = A * w0 + B * w2;
+    // coefficient of g_k in dPhi: gamma_k; times -2/q_k
+    const R k0 = (A * w0 - w0 * E) * R(-2) * r0;
+    const R k1 = (-w1 * E) * R(-2) * r1;
+    const R k2 = (B * w2 - w2 * E) * R(-2) * r2;
+    // dIS / d(a,b), d(b,c), d(c,d)
+    const R i0a = R(26) * (a - b) + R(6) * f0, i0b = R(-26) * (a - b) - R(18) * f0;
+    const R i1b = R(26) * (b - c) + R(6) * f1, i1c = R(-26) * (b - c) + R(6) * f1;
+    const R i2c = R(26) * (c - d) + R(18) * f2, i2d = R(-26) * (c - d) - R(6) * f2;
+    gabcd[0] = w0 * R(1.0 / 3.0) + k0 * i0a;
+    gabcd[1] = w0 * R(-2.0 / 3.0) + (w2 - R(0.5)) * R(1.0 / 6.0) + k0 * i0b + k1 * i1b;
+    gabcd[2] = w0 * R(1.0 / 3.0) + (w2 - R(0.5)) * R(-2.0 / 6.0) + k1 * i1c + k2 * i2c;
+    gabcd[3] = (w2 - R(0.5)) * R(1.0 / 6.0) + k2 * i2d;
+    *ge = k0 + k1 + k2;
+}
+
+template <typename R>
+__device__ __forceinline__ void grad_weno5(const R* u7, R inv_dx, R floor12, R* gm, R* gp)
+{
+    R D[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) D[m] = u7[m + 1] - u7[m];  // D[m] = D_{m-3}
+    R S[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) S[j] = D[j + 1] - D[j];    // S[j] = S_{j-2}
+    // the central part (shared by both sides): (-D_-2 + 7 D_-1 + 7 D_0 - D_1)/12
+    const R cw[4] = {R(-1.0 / 12.0), R(7.0 / 12.0), R(7.0 / 12.0), R(-1.0 / 12.0)};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        add_D(gm, q - 2, cw[q] * inv_dx);
+        add_D(gp, q - 2, cw[q] * inv_dx);
+    }
+    // regulariser e = 1.2e-5 max(D^2 over the side's five differences) + floor;
+    // argmax frozen (the first of equal values)
+    int mL = 0, mR = 1;
+#pragma unroll
+    for (int m = 1; m < 5; ++m)
+        if (D[m] * D[m] > D[mL] * D[mL]) mL = m;
+#pragma unroll
+    for (int m = 2; m < 6; ++m)
+        if (D[m] * D[m] > D[mR] * D[mR]) mR = m;
+    const R eL = R(1.2e-5) * D[mL] * D[mL] + floor12;
+    const R eR = R(1.2e-5) * D[mR] * D[mR] + floor12;
+    R g4[4], ge;
+    // p- = (cen - Phi(S_-2, S_-1, S_0, S_1)) / dx
+    weno_phi_grad(S[0], S[1], S[2], S[3], eL, g4, &ge);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) add_S(gm, q - 2, -g4[q] * inv_dx);
+    add_D(gm, mL - 3, -ge * R(2.4e-5) * D[mL] * inv_dx);
+    // p+ = (cen + Phi(S_2, S_1, S_0, S_-1)) / dx
+    weno_phi_grad(S[4], S[3], S[2], S[1], eR, g4, &ge);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) add_S(gp, 2 - q, g4[q] * inv_dx);
+    add_D(gp, mR - 3, ge * R(2.4e-5) * D[mR] * inv_dx);
+}
+
+template <int SCHEME, typename R>
+__device__ __forceinline__ void window_grad(const R* u7, R inv_dx, R floor12, R* gm, R* gp)
+{
+#pragma unroll
+    for (int o = 0; o < 7; ++o) gm[o] = gp[o] = R(0);
+    if constexpr (SCHEME == UPWIND1) grad_upwind1(inv_dx, gm, gp);
+    else if constexpr (SCHEME == ENO2) grad_eno<R, 2>(u7, inv_dx, gm, gp);
+    else if constexpr (SCHEME == ENO3) grad_eno<R, 3>(u7, inv_dx, gm, gp);
+    else grad_weno5(u7, inv_dx, floor12, gm, gp);
+}
+
+// ---------------------------------------------------------------------------
+// dH/dp_k (frozen input selections, sign(0) = +1) and dH/dprm_j.
+__device__ __forceinline__ float sgn1(float v) { return v >= 0.f ? 1.f : -1.f; }
+__device__ __forceinline__ double sgn1(double v) { return v >= 0.0 ? 1.0 : -1.0; }
+
+template <int DYN, int NDIM, typename R>
+__device__ __forceinline__ void ham_grad(const R* x, const R* p, const R* prm, R s, R c, R* hp,
+                                         R* hprm)
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) hprm[j] = R(0);
+    if constexpr (DYN == NORMAL_SPEED) {
+        R n2 = R(0);
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) n2 += p[k] * p[k];
+        const R n = rsqrt_(n2);
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) hp[k] = n > R(0) ? prm[0] * p[k] / n : R(0);
+        hprm[0] = n;
+    } else if constexpr (DYN == TRANSLATE) {
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+            hp[k] = prm[k];
+            if (k < 4) hprm[k] = p[k];
+        }
+    } else if constexpr (DYN == AIR3D) {
+        const R ve = prm[0], vp = prm[1], um = prm[2], dm = prm[3];
+        const R s1 = p[0] * x[1] - p[1] * x[0] - p[2];
+        const R g1 = sgn1(s1), g3 = sgn1(p[2]);
+        hp[0] = -((-ve + vp * c) + um * g1 * x[1]);
+        hp[1] = -(vp * s - um * g1 * x[0]);
+        hp[2] = um * g1 + dm * g3;
+        hprm[0] = p[0];
+        hprm[1] = -(p[0] * c + p[1] * s);
+        hprm[2] = -rabs(s1);
+        hprm[3] = rabs(p[2]);
+    } else if constexpr (DYN == CAR4D) {
+        const R v = x[3];
+        hp[0] = -v * c;
+        hp[1] = -v * s;
+        hp[2] = prm[0] * sgn1(p[2]);
+        hp[3] = prm[1] * sgn1(p[3]);
+        hprm[0] = rabs(p[2]);
+        hprm[1] = rabs(p[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) hp[k] = p[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+struct AdjAcc {        // FP64 accumulators (device)
+    double hprm[4];    // sum_i w_i (-dH/dprm_j)
+    double alpha[4];   // sum_i w_i (p+_k - p-_k)/2
+    double dt;         // sum_i lam_v,i c_l L_i
+    double pad[7];
+};
+
+template <typename R>
+struct AdjArgs {
+    const R* u;        // stage input (stencil)
+    const R* phin;     // phi^n (pointwise; NULL when c_n == 0)
+    const R* target;   // read when tube
+    const R* lam;      // dLoss/d out
+    R* lam_v;          // out: dLoss/dv per node
+    R* contrib;        // out: NDIM * 7 coefficients per node (axis-major)
+    R* lam_u;          // ghost folds (atomics) here; pass B adds the rest
+    R* lam_n;          // pass B: += c_n lam_v (may equal lam_u)
+    R* lam_g;          // tube: += lam where the min took the target (nullable)
+    AdjAcc* acc;
+    int n[LSP_MAXD];
+    int stride[LSP_MAXD];
+    int periodic[LSP_MAXD];
+    R inv_dx[LSP_MAXD];
+    R lo[LSP_MAXD];
+    R h[LSP_MAXD];
+    R alpha[LSP_MAXD];
+    R prm[LSP_NPARAM];
+    R dt, c_n, c_s, c_l;
+    int tube;
+    int npts;
+};
+
+template <int NDIM, int SCHEME, int DYN, typename R>
+__global__ void __launch_bounds__(256) adj_stage_a(AdjArgs<R> a)
+{
+    constexpr int G = ghost_width(SCHEME);
+    double acc_h[4] = {0, 0, 0, 0}, acc_a[4] = {0, 0, 0, 0}, acc_dt = 0.0;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < a.npts;
+         idx += gridDim.x * blockDim.x) {
+        int c[NDIM];
+        {
+            int r = idx;
+#pragma unroll
+            for (int k = NDIM - 1; k >= 0; --k) {
+                c[k] = r % a.n[k];
+                r /= a.n[k];
+            }
+        }
+        R x[NDIM], pm[NDIM], pp[NDIM], pbar[NDIM], win[NDIM][7];
+        R diss = R(0);
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+            R u[7];
+            load_window<R, 3>(a.u, idx, c[k], a.n[k], a.stride[k], a.periodic[k], u);
+#pragma unroll
+            for (int o = 0; o < 7; ++o) win[k][o] = u[o];
+            deriv_fast<SCHEME>(u + (3 - G), a.inv_dx[k], weno_floor12(a.inv_dx[k]), pm[k], pp[k]);
+            pbar[k] = R(0.5) * (pp[k] + pm[k]);
+            diss += a.alpha[k] * R(0.5) * (pp[k] - pm[k]);
+            x[k] = a.lo[k] + R(c[k]) * a.h[k];
+        }
+        R sth = R(0), cth = R(1);
+        if constexpr (DYN == AIR3D || DYN == CAR4D) rsincos(x[2], &sth, &cth);
+        const R H = hamiltonian_sc<DYN, NDIM>(x, pbar, a.prm, sth, cth);
+        const R L = -(H - diss);
+        R v = a.c_s * a.u[idx] + (a.c_l * a.dt) * L;
+        if (a.phin) v += a.c_n * a.phin[idx];
+        R lv = a.lam[idx];
+        if (a.tube) {
+            const R g = a.target[idx];
+            if (g < v) {  // the min took the target
+                if (a.lam_g) a.lam_g[idx] += lv;
+                lv = R(0);
+            }
+        }
+        a.lam_v[idx] = lv;
+        const R w = a.c_l * a.dt * lv;
+        acc_dt += (double)(a.c_l * lv) * (double)L;
+        R hp[NDIM], hprm[4];
+        ham_grad<DYN, NDIM>(x, pbar, a.prm, sth, cth, hp, hprm);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc_h[j] += (double)(w * -hprm[j]);
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+            acc_a[k] += (double)(w * R(0.5) * (pp[k] - pm[k]));
+            R gm[7], gp[7];
+            window_grad<SCHEME>(win[k] + 0, a.inv_dx[k], weno_floor12(a.inv_dx[k]), gm, gp);
+            const R sp = w * (R(-0.5) * hp[k] + R(0.5) * a.alpha[k]);
+            const R sm = w * (R(-0.5) * hp[k] - R(0.5) * a.alpha[k]);
+            R* out = a.contrib + ((long long)k * a.npts + idx) * 7;
+            const int n = a.n[k], s = a.stride[k];
+#pragma unroll
+            for (int o = -3; o <= 3; ++o) {
+                R cf = sp * gp[o + 3] + sm * gm[o + 3];
+                const int j = c[k] + o;
+                if (!a.periodic[k] && (j < 0 || j >= n)) {
+                    // ghost of an extrapolated axis: u_j = (1+q) u_b - q u_b', fold now
+                    if (cf != R(0)) {
+                        const long long line0 = (long long)idx - (long long)c[k] * s;
+                        if (j < 0) {
+                            const R q = R(-j);
+                            atomicAdd(a.lam_u + line0, (R(1) + q) * cf);
+                            atomicAdd(a.lam_u + line0 + s, -q * cf);
+                        } else {
+                            const R q = R(j - n + 1);
+                            atomicAdd(a.lam_u + line0 + (long long)(n - 1) * s, (R(1) + q) * cf);
+                            atomicAdd(a.lam_u + line0 + (long long)(n - 2) * s, -q * cf);
+                        }
+                    }
+                    cf = R(0);
+                }
+                out[o + 3] = cf;
+            }
+        }
+    }
+    // block reductions of the accumulators, one FP64 atomic each per block
+    __shared__ double red[9][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double vals[9] = {acc_h[0], acc_h[1], acc_h[2], acc_h[3], acc_a[0], acc_a[1], acc_a[2], acc_a[3], acc_dt};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        double v = vals[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[q][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        double* dst = threadIdx.x < 4 ? a.acc->hprm + threadIdx.x
+                    : threadIdx.x < 8 ? a.acc->alpha + (threadIdx.x - 4)
+                                      : &a.acc->dt;
+        if (v != 0.0) atomicAdd(dst, v);
+    }
+}
+
+template <int NDIM, typename R>
+__global__ void __launch_bounds__(256) adj_stage_b(AdjArgs<R> a)
+{
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < a.npts;
+         idx += gridDim.x * blockDim.x) {
+        int c[NDIM];
+        {
+            int r = idx;
+#pragma unroll
+            for (int k = NDIM - 1; k >= 0; --k) {
+                c[k] = r % a.n[k];
+                r /= a.n[k];
+            }
+        }
+        const R lv = a.lam_v[idx];
+        R acc = a.c_s * lv;
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+            const int n = a.n[k], s = a.stride[k];
+            const R* ck = a.contrib + (long long)k * a.npts * 7;
+#pragma unroll
+            for (int o = -3; o <= 3; ++o) {
+                int i = c[k] - o;  // the node whose window offset o is this node
+                if (i < 0 || i >= n) {
+                    if (!a.periodic[k]) continue;
+                    i = i < 0 ? i + n : i - n;
+                }
+                const long long node = (long long)idx + (long long)(i - c[k]) * s;
+                acc += ck[node * 7 + (o + 3)];
+            }
+        }
+        if (a.lam_n != a.lam_u && a.lam_n) a.lam_n[idx] += a.c_n * lv;
+        else acc += a.c_n * lv;
+        a.lam_u[idx] += acc;
+    }
+}
+
+// First node (C order) whose per-node LF bound on axis k equals alpha_k:
+// the node the GLF coefficient's derivative is taken at.
+template <int DYN>
+__global__ void __launch_bounds__(256) alpha_argmax_kernel(GridGeom g, const double* alpha,
+                                                          unsigned long long* out)
+{
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < g.npts;
+         idx += (long long)gridDim.x * blockDim.x) {
+        double x[LSP_MAXD] = {0.0, 0.0, 0.0, 0.0};
+        long long r = idx;
+        for (int k = g.ndim - 1; k >= 0; --k) {
+            x[k] = g.lo[k] + (double)(r % g.n[k]) * g.h[k];
+            r /= g.n[k];
+        }
+        for (int k = 0; k < g.ndim; ++k)
+            if (partial_bound<DYN>(x, k, g.prm) == alpha[k])
+                atomicMin(out + k, (unsigned long long)idx);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Loss of the differentiation workload on the device:
+//   sum_i H_eps(-phi_i) dV + sum_q phi(x_q),  H_eps(s) = 1/(1 + exp(-s/eps))
+// with multilinear interpolation at the query states (periodic axes wrap,
+// the others clamp), and its gradient.
+template <typename R, int NDIM>
+struct InterpArgs {
+    const R* phi;
+    const R* queries;  // nq x NDIM
+    int nq;
+    int n[LSP_MAXD];
+    int stride[LSP_MAXD];
+    int periodic[LSP_MAXD];
+    double lo[LSP_MAXD], h[LSP_MAXD];
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) loss_volume_kernel(const R* phi, int npts, double inv_eps,
+                                                         double dV, double* value, R* grad)
+{
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += gridDim.x * blockDim.x) {
+        const double Hs = 1.0 / (1.0 + exp((double)phi[i] * inv_eps));  // H_eps(-phi)
+        acc += Hs * dV;
+        if (grad) grad[i] = R(-Hs * (1.0 - Hs) * inv_eps * dV);
+    }
+    __shared__ double red[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+        atomicAdd(value, v);
+    }
+}
+
+template <typename R, int NDIM>
+__global__ void __launch_bounds__(128) loss_query_kernel(InterpArgs<R, NDIM> a, double* value,
+                                                        R* grad)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.nq) return;
+    int i0[NDIM], i1[NDIM];
+    double f[NDIM];
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) {
+        double t = ((double)a.queries[q * NDIM + k] - a.lo[k]) / a.h[k];
+        const int n = a.n[k];
+        if (a.periodic[k]) {
+            const double fl = floor(t);
+            f[k] = t - fl;
+            int b = (int)fl % n;
+            if (b < 0) b += n;
+            i0[k] = b;
+            i1[k] = (b + 1) % n;
+        } else {
+            t = fmin(fmax(t, 0.0), (double)(n - 1));
+            int b = (int)floor(t);
+            if (b > n - 2) b = n - 2;
+            f[k] = t - b;
+            i0[k] = b;
+            i1[k] = b + 1;
+        }
+    }
+    double val = 0.0;
+    for (int corner = 0; corner < (1 << NDIM); ++corner) {
+        double w = 1.0;
+        long long off = 0;
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+            const int bit = (corner >> (NDIM - 1 - k)) & 1;
+            w *= bit ? f[k] : 1.0 - f[k];
+            off += (long long)(bit ? i1[k] : i0[k]) * a.stride[k];
+        }
+        val += w * (double)a.phi[off];
+        if (grad) atomicAdd(grad + off, R(w));
+    }
+    atomicAdd(value, val);
+}
+
+}  // namespace lsp

@@ -1,0 +1,97 @@
+// adjoint.inl -- instantiations of the adjoint stage kernels and the loss
+// kernels for one precision LSP_REAL (included by adjoint_f32.cu /
+// adjoint_f64.cu).
+#include "adjoint.cuh"
+#include "launch.h"
+
+namespace lsp {
+
+static inline int adj_blocks(long long npts)
+{
+    long long b = (npts + 255) / 256;
+    const long long cap = 152LL * 16;
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+template <int NDIM, int SCHEME>
+static cudaError_t adj_dyn(int dyn, const AdjArgs<LSP_REAL>& a, cudaStream_t s)
+{
+    const int nb = adj_blocks(a.npts);
+    switch (dyn) {
+    case NORMAL_SPEED: adj_stage_a<NDIM, SCHEME, NORMAL_SPEED, LSP_REAL><<<nb, 256, 0, s>>>(a); break;
+    case TRANSLATE: adj_stage_a<NDIM, SCHEME, TRANSLATE, LSP_REAL><<<nb, 256, 0, s>>>(a); break;
+    case AIR3D:
+        if constexpr (NDIM == 3) { adj_stage_a<3, SCHEME, AIR3D, LSP_REAL><<<nb, 256, 0, s>>>(a); break; }
+        return cudaErrorInvalidValue;
+    case CAR4D:
+        if constexpr (NDIM == 4) { adj_stage_a<4, SCHEME, CAR4D, LSP_REAL><<<nb, 256, 0, s>>>(a); break; }
+        return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    adj_stage_b<NDIM, LSP_REAL><<<nb, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NDIM>
+static cudaError_t adj_scheme(int scheme, int dyn, const AdjArgs<LSP_REAL>& a, cudaStream_t s)
+{
+    switch (scheme) {
+    case UPWIND1: return adj_dyn<NDIM, UPWIND1>(dyn, a, s);
+    case ENO2: return adj_dyn<NDIM, ENO2>(dyn, a, s);
+    case ENO3: return adj_dyn<NDIM, ENO3>(dyn, a, s);
+    case WENO5: return adj_dyn<NDIM, WENO5>(dyn, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <>
+cudaError_t launch_adjoint_stage<LSP_REAL>(int ndim, int scheme, int dyn,
+                                           const AdjArgs<LSP_REAL>& a, cudaStream_t s)
+{
+    switch (ndim) {
+    case 1: return adj_scheme<1>(scheme, dyn, a, s);
+    case 2: return adj_scheme<2>(scheme, dyn, a, s);
+    case 3: return adj_scheme<3>(scheme, dyn, a, s);
+    case 4: return adj_scheme<4>(scheme, dyn, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int NDIM>
+static void loss_q(const LossArgs<LSP_REAL>& L, double* value, LSP_REAL* grad, cudaStream_t s)
+{
+    InterpArgs<LSP_REAL, NDIM> a;
+    a.phi = L.phi;
+    a.queries = L.queries;
+    a.nq = L.nq;
+    for (int k = 0; k < LSP_MAXD; ++k) {
+        a.n[k] = L.n[k];
+        a.stride[k] = L.stride[k];
+        a.periodic[k] = L.periodic[k];
+        a.lo[k] = L.lo[k];
+        a.h[k] = L.h[k];
+    }
+    loss_query_kernel<LSP_REAL, NDIM><<<(L.nq + 127) / 128, 128, 0, s>>>(a, value, grad);
+}
+
+template <>
+cudaError_t launch_loss<LSP_REAL>(const LossArgs<LSP_REAL>& L, double* value, LSP_REAL* grad,
+                                  cudaStream_t s)
+{
+    loss_volume_kernel<LSP_REAL><<<adj_blocks(L.npts), 256, 0, s>>>(L.phi, L.npts, L.inv_eps,
+                                                                      L.dV, value, grad);
+    cudaError_t e = cudaGetLastError();
+    if (e || L.nq <= 0) return e;
+    switch (L.ndim) {
+    case 1: loss_q<1>(L, value, grad, s); break;
+    case 2: loss_q<2>(L, value, grad, s); break;
+    case 3: loss_q<3>(L, value, grad, s); break;
+    case 4: loss_q<4>(L, value, grad, s); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lsp

@@ -18,6 +18,45 @@ cudaError_t launch_prange(int ndim, int scheme, const StageArgs<R>& a, cudaStrea
 // State-only global-LF coefficients (FP64).
 cudaError_t launch_alpha_state(int dyn, const GridGeom& g, unsigned long long* out, cudaStream_t s);
 
+struct Tile;
+
+// Tiled fused stage for 3-D and 4-D FP32 grids (stage_tiled.cuh); one
+// instantiation set per occupancy target MINB (stage_tiled_m*.cu).
+template <int MINB>
+cudaError_t launch_stage_tiled_m(int ndim, int scheme, int dyn, const StageArgs<float>& a,
+                                 const Tile& t, cudaStream_t s);
+cudaError_t launch_stage_tiled(int ndim, int scheme, int dyn, const StageArgs<float>& a,
+                               const Tile& t, cudaStream_t s);
+bool tile_valid(int ndim, int scheme, const Tile& t, const int* n);
+
+// Batched stages (batched.cu): RK2/RK3, FP32, problems of 2 to 4 dimensions.
+struct BatchProblem;
+cudaError_t launch_batched(int scheme, const BatchProblem* probs, const int* block_prob, int nblocks,
+                           int step, int stage, int rk, cudaStream_t s);
+void batch_tile_dims(int* tb, int* ta);
+bool batch_supported(int ndim, int dyn);
+
+// Adjoint of one stage (adjoint.cuh): pass A + pass B.
+template <typename R> struct AdjArgs;
+template <typename R>
+cudaError_t launch_adjoint_stage(int ndim, int scheme, int dyn, const AdjArgs<R>& a,
+                                 cudaStream_t s);
+cudaError_t launch_alpha_argmax(int dyn, const GridGeom& g, const double* alpha,
+                                unsigned long long* out, cudaStream_t s);
+
+// Loss of the differentiation workload (value accumulated into *value).
+template <typename R>
+struct LossArgs {
+    const R* phi;
+    const R* queries;
+    int nq, ndim, npts;
+    int n[LSP_MAXD], stride[LSP_MAXD], periodic[LSP_MAXD];
+    double lo[LSP_MAXD], h[LSP_MAXD];
+    double inv_eps, dV;
+};
+template <typename R>
+cudaError_t launch_loss(const LossArgs<R>& L, double* value, R* grad, cudaStream_t s);
+
 // Is there a kernel for this combination?
 bool stage_supported(int ndim, int scheme, int dyn);
 

@@ -4,11 +4,17 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
+#include <type_traits>
+#include <vector>
 
 #include "../../include/lsp.h"
+#include "adjoint.cuh"
+#include "batched.h"
 #include "launch.h"
 #include "stage_generic.cuh"
+#include "stage_tiled.cuh"
 
 struct lsp_grid {
     int ndim = 0;
@@ -22,6 +28,11 @@ struct lsp_grid {
     double prm[LSP_NPARAM] = {0, 0, 0, 0, 0, 0, 0, 0};
     double alpha[LSP_MAXD] = {0, 0, 0, 0};
     bool alpha_state = false;  // alpha known on the host (state-only bound)
+
+    // tile of the tiled 3-D/4-D FP32 stage kernel: mode 0 = default shape,
+    // 1 = set explicitly (or by the autotuner), -1 = use the generic kernel
+    int tile_mode = 0;
+    lsp::Tile tile{0, 0, 0, 3};
 
     // cached CUDA graph of the last lsp_hj_solve with use_graph
     cudaGraphExec_t gexec = nullptr;
@@ -71,8 +82,9 @@ lsp_status check_opts(const lsp_grid* g, const lsp_solve_opts* o)
     if (o->scheme < LSP_UPWIND1 || o->scheme > LSP_WENO5) return fail(LSP_EINVAL, "bad scheme");
     if (o->dtype != LSP_F32 && o->dtype != LSP_F64) return fail(LSP_EINVAL, "bad dtype");
     if (!(o->cfl > 0.0 && o->cfl <= 1.0)) return fail(LSP_EINVAL, "cfl must be in (0, 1]");
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 5; ++i)
         if (o->reserved[i]) return fail(LSP_EINVAL, "reserved option fields must be zero");
+    if (o->batch_chunk < 0) return fail(LSP_EINVAL, "batch_chunk must be >= 0");
     const int G = lsp::ghost_width(o->scheme);
     for (int k = 0; k < g->ndim; ++k)
         if (g->n[k] < 2 * G + 1)
@@ -106,6 +118,35 @@ double cfl_dt_host(const lsp_grid* g, double cfl, double t, double t_final)
     double dt = (s > 0.0) ? cfl / s : (t_final - t);
     if (t_final - t < dt) dt = t_final - t;
     return dt;
+}
+
+// Default tile: 32 x 8 threads over the two fastest axes, the march along
+// the third split into chunks so that at least ~2 waves of 2 CTAs per SM
+// are launched.
+lsp::Tile default_tile(const lsp_grid* g)
+{
+    const int d = g->ndim;
+    lsp::Tile t;
+    t.tb = 32;
+    t.ta = 8;
+    t.minb = 3;
+    const long long nplane = (long long)((g->n[d - 1] + t.tb - 1) / t.tb) *
+                             ((g->n[d - 2] + t.ta - 1) / t.ta) * (d == 4 ? g->n[0] : 1);
+    long long nch = (2LL * 2 * 152 + nplane - 1) / nplane;
+    const int nS = g->n[d - 3];
+    if (nch > nS / 4) nch = nS / 4;
+    if (nch < 1) nch = 1;
+    t.ch = (int)((nS + nch - 1) / nch);
+    return t;
+}
+
+// The tile the FP32 3-D/4-D stages use, or ch = 0 for the generic kernel.
+lsp::Tile tile_in_effect(const lsp_grid* g, const lsp_solve_opts* o)
+{
+    lsp::Tile none{0, 0, 0, 0};
+    if (o->dtype != LSP_F32 || (g->ndim != 3 && g->ndim != 4) || g->tile_mode < 0) return none;
+    lsp::Tile t = g->tile_mode == 1 ? g->tile : default_tile(g);
+    return lsp::tile_valid(g->ndim, o->scheme, t, g->n) ? t : none;
 }
 
 template <typename R>
@@ -153,6 +194,14 @@ lsp_status enqueue_stage(const lsp_grid* g, const lsp_solve_opts* o, lsp::Ctl* c
         if (e != cudaSuccess) return cuda_fail(e, "memset alpha");
         e = lsp::launch_prange<R>(g->ndim, o->scheme, a, st);
         if (e != cudaSuccess) return cuda_fail(e, "costate range kernel");
+    }
+    if constexpr (std::is_same<R, float>::value) {
+        const lsp::Tile t = tile_in_effect(g, o);
+        if (t.ch > 0) {
+            e = lsp::launch_stage_tiled(g->ndim, o->scheme, g->dyn, a, t, st);
+            if (e != cudaSuccess) return cuda_fail(e, "tiled stage kernel");
+            return LSP_OK;
+        }
     }
     e = lsp::launch_stage<R>(g->ndim, o->scheme, g->dyn, a, st);
     if (e != cudaSuccess) return cuda_fail(e, "stage kernel");
@@ -561,6 +610,708 @@ lsp_status lsp_hj_solve(lsp_grid* g, const lsp_solve_opts* o, void* phi, const v
     if (stats) *stats = sts;
     if (o->check_finite) return read_flags(ws, st);
     return LSP_OK;
+}
+
+lsp_status lsp_set_tile(lsp_grid* g, int tb, int ta, int ch, int minb)
+{
+    if (!g) return fail(LSP_EINVAL, "grid is NULL");
+    if (g->gexec) {
+        cudaGraphExecDestroy(g->gexec);
+        g->gexec = nullptr;
+    }
+    if (tb < 0) {
+        g->tile_mode = -1;
+        return LSP_OK;
+    }
+    if (tb == 0 && ta == 0 && ch == 0) {
+        g->tile_mode = 0;
+        return LSP_OK;
+    }
+    lsp::Tile t{tb, ta, ch, minb};
+    if (!lsp::tile_valid(g->ndim, LSP_WENO5, t, g->n))
+        return fail(LSP_EINVAL, "tile %dx%dx%d (%d CTAs/SM) is not valid for this grid", tb, ta,
+                    ch, minb);
+    g->tile = t;
+    g->tile_mode = 1;
+    return LSP_OK;
+}
+
+lsp_status lsp_get_tile(const lsp_grid* g, const lsp_solve_opts* o, int* tb, int* ta, int* ch,
+                        int* minb)
+{
+    lsp_status s = check_opts(g, o);
+    if (s) return s;
+    if (!tb || !ta || !ch || !minb) return fail(LSP_EINVAL, "NULL argument");
+    const lsp::Tile t = tile_in_effect(g, o);
+    if (t.ch == 0) {
+        *tb = *ta = *ch = *minb = -1;
+    } else {
+        *tb = t.tb;
+        *ta = t.ta;
+        *ch = t.ch;
+        *minb = t.minb;
+    }
+    return LSP_OK;
+}
+
+lsp_status lsp_autotune(lsp_grid* g, const lsp_solve_opts* o, const void* phi, void* ws,
+                        size_t ws_size, void* stream, int* tb_out, int* ta_out, int* ch_out,
+                        int* minb_out)
+{
+    lsp_status s = check_opts(g, o);
+    if (!s) s = check_field(phi, "phi");
+    if (!s) s = check_ws(g, o, ws, ws_size);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (o->dtype != LSP_F32 || (g->ndim != 3 && g->ndim != 4)) {
+        g->tile_mode = -1;
+        if (tb_out) *tb_out = -1;
+        if (ta_out) *ta_out = -1;
+        if (ch_out) *ch_out = -1;
+        if (minb_out) *minb_out = -1;
+        return LSP_OK;
+    }
+    if (!g->alpha_state) return fail(LSP_EUNSUPPORTED, "autotune needs state-only LF bounds");
+    const int d = g->ndim;
+    const int shapes[][2] = {{32, 8}, {32, 4}, {16, 8}, {16, 16}, {64, 4}, {32, 6}, {48, 4}};
+    const int splits[] = {1, 2, 3, 4, 6, 8, 12};
+    lsp::Ctl* ctl = (lsp::Ctl*)ws;
+    float* w1 = (float*)((char*)ws + lsp::kCtlBytes);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return fail(LSP_ECUDA, "event create");
+    lsp_grid trial = *g;
+    trial.gexec = nullptr;
+    trial.capture_stream = nullptr;
+    float best_ms = 1e30f;
+    lsp::Tile best{0, 0, 0, 0};
+    const double dt = cfl_dt_host(g, o->cfl, 0.0, INFINITY);
+    for (const auto& sh : shapes) {
+        for (int cand = 0; cand < 21; ++cand) {
+            const int sp = splits[cand % 7];
+            const int minb = 2 + cand / 7;
+            const int nS = g->n[d - 3];
+            lsp::Tile t{sh[0], sh[1], (nS + sp - 1) / sp, minb};
+            if (!lsp::tile_valid(d, o->scheme, t, g->n)) continue;
+            trial.tile = t;
+            trial.tile_mode = 1;
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, st);
+                s = enqueue_stage<float>(&trial, o, ctl, (const float*)phi, nullptr, nullptr, w1,
+                                         dt, 0.0, 1.0, 1.0, false, st);
+                cudaEventRecord(e1, st);
+                if (s) break;
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0 && ms < ms_min) ms_min = ms;  // first run warms up
+            }
+            if (s) break;
+            if (ms_min < best_ms) {
+                best_ms = ms_min;
+                best = t;
+            }
+        }
+        if (s) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s) return s;
+    if (best.ch == 0) return fail(LSP_EUNSUPPORTED, "no valid tile for this grid");
+    g->tile = best;
+    g->tile_mode = 1;
+    if (g->gexec) {
+        cudaGraphExecDestroy(g->gexec);
+        g->gexec = nullptr;
+    }
+    if (tb_out) *tb_out = best.tb;
+    if (ta_out) *ta_out = best.ta;
+    if (ch_out) *ch_out = best.ch;
+    if (minb_out) *minb_out = best.minb;
+    return LSP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct BatchPlanEntry {
+    int p;  // index in the caller's arrays
+    int nsteps;
+    double dt, dt_last;
+    int nbx, nby, nchunks, ch, nblocks;
+    size_t field_bytes;  // one stage field, rounded to 256
+};
+
+// Prefix the thread's last-error text with the problem index.
+lsp_status fail_problem(lsp_status s, int i)
+{
+    char tmp[sizeof(g_err)];
+    std::snprintf(tmp, sizeof(tmp), "%s", g_err);
+    return fail(s, "problem %d: %s", i, tmp);
+}
+
+lsp_status batch_check(int nprob, lsp_grid* const* grids, const lsp_solve_opts* o)
+{
+    if (nprob < 1) return fail(LSP_EINVAL, "nprob must be >= 1");
+    if (!grids) return fail(LSP_EINVAL, "grids is NULL");
+    if (!o) return fail(LSP_EINVAL, "opts is NULL");
+    if (o->dtype != LSP_F32) return fail(LSP_EUNSUPPORTED, "batched solves are FP32");
+    if (o->rk_order != 2 && o->rk_order != 3)
+        return fail(LSP_EUNSUPPORTED, "batched solves use TVD-RK2 or RK3");
+    for (int i = 0; i < nprob; ++i) {
+        const lsp_grid* g = grids[i];
+        lsp_status s = check_opts(g, o);
+        if (s) return fail_problem(s, i);
+        if (!g->alpha_state)
+            return fail(LSP_EUNSUPPORTED, "problem %d: batched solves need state-only LF bounds", i);
+        if (!lsp::batch_supported(g->ndim, g->dyn))
+            return fail(LSP_EUNSUPPORTED, "problem %d: no batched kernel for ndim=%d dyn=%d", i,
+                        g->ndim, g->dyn);
+    }
+    return LSP_OK;
+}
+
+// Tile grid and field sizes of every problem; the total workspace bytes.
+void batch_geometry(int nprob, lsp_grid* const* grids, const lsp_solve_opts* o,
+                    std::vector<BatchPlanEntry>& plan, size_t* bytes, long long* total_blocks)
+{
+    int tb, ta;
+    lsp::batch_tile_dims(&tb, &ta);
+    const int chunk = o->batch_chunk > 0 ? o->batch_chunk : 32;
+    plan.resize(nprob);
+    size_t fields = 0;
+    long long blocks = 0;
+    for (int i = 0; i < nprob; ++i) {
+        const lsp_grid* g = grids[i];
+        BatchPlanEntry& e = plan[i];
+        const int d = g->ndim;
+        e.p = i;
+        e.nsteps = 0;
+        e.dt = e.dt_last = 0.0;
+        e.nbx = (g->n[d - 1] + tb - 1) / tb;
+        e.nby = (g->n[d - 2] + ta - 1) / ta;
+        if (d >= 3) {
+            const int nS = g->n[d - 3];
+            e.ch = std::min(chunk, nS);
+            e.nchunks = (nS + e.ch - 1) / e.ch;
+        } else {
+            e.ch = 1;
+            e.nchunks = 1;
+        }
+        e.nblocks = e.nbx * e.nby * e.nchunks * (d == 4 ? g->n[0] : 1);
+        e.field_bytes = round256((size_t)g->npts * sizeof(float));
+        fields += nfields(o->rk_order) * e.field_bytes;
+        blocks += e.nblocks;
+    }
+    *total_blocks = blocks;
+    *bytes = lsp::kCtlBytes + round256((size_t)nprob * sizeof(lsp::BatchProblem)) +
+             round256((size_t)blocks * sizeof(int)) + fields;
+}
+
+}  // namespace
+
+extern "C" {
+
+lsp_status lsp_batched_workspace_size(int nprob, lsp_grid* const* grids, const lsp_solve_opts* o,
+                                      size_t* bytes)
+{
+    if (!bytes) return fail(LSP_EINVAL, "bytes is NULL");
+    lsp_status s = batch_check(nprob, grids, o);
+    if (s) return s;
+    std::vector<BatchPlanEntry> plan;
+    long long blocks = 0;
+    batch_geometry(nprob, grids, o, plan, bytes, &blocks);
+    return LSP_OK;
+}
+
+lsp_status lsp_hj_solve_batched(int nprob, lsp_grid* const* grids, const lsp_solve_opts* o,
+                                void* const* phis, const void* const* targets,
+                                const double* t_final, void* ws, size_t ws_size,
+                                lsp_solve_stats* stats, void* stream)
+{
+    lsp_status s = batch_check(nprob, grids, o);
+    if (s) return s;
+    if (!phis || !t_final) return fail(LSP_EINVAL, "phis and t_final must not be NULL");
+    if (o->tube && !targets) return fail(LSP_EINVAL, "targets is NULL with tube on");
+    for (int i = 0; i < nprob; ++i) {
+        if ((s = check_field(phis[i], "phi"))) return fail_problem(s, i);
+        if (o->tube && (s = check_field(targets[i], "target"))) return fail_problem(s, i);
+        if (!std::isfinite(t_final[i])) return fail(LSP_EINVAL, "problem %d: t_final not finite", i);
+    }
+    if (!ws || !aligned16(ws)) return fail(LSP_EINVAL, "workspace must be non-NULL and 16-byte aligned");
+    std::vector<BatchPlanEntry> plan;
+    size_t need = 0;
+    long long total_blocks = 0;
+    batch_geometry(nprob, grids, o, plan, &need, &total_blocks);
+    if (ws_size < need) return fail(LSP_ENOMEM, "workspace has %zu bytes, needs %zu", ws_size, need);
+    if (total_blocks > 0x7fffffffLL) return fail(LSP_EINVAL, "too many tiles");
+
+    // per-problem FP64 time loop (the same as a single solve's)
+    for (auto& e : plan) {
+        const lsp_grid* g = grids[e.p];
+        const double tf = t_final[e.p];
+        const double t_stop = tf - 1e-12 * std::fabs(tf);
+        double t = 0.0;
+        e.dt = cfl_dt_host(g, o->cfl, 0.0, INFINITY);
+        while (t < t_stop) {
+            const double dt = cfl_dt_host(g, o->cfl, t, tf);
+            if (!(dt > 0.0)) return fail(LSP_EINVAL, "problem %d: non-positive CFL step", e.p);
+            e.dt_last = dt;
+            t += dt;
+            e.nsteps++;
+        }
+        if (stats) {
+            lsp_solve_stats& st = stats[e.p];
+            st.steps = e.nsteps;
+            st.stages = (int64_t)e.nsteps * o->rk_order;
+            st.dt_min = e.nsteps ? std::fmin(e.dt, e.dt_last) : INFINITY;
+            st.dt_max = e.nsteps ? std::fmax(e.dt, e.dt_last) : 0.0;
+            st.t_end = t;
+        }
+    }
+    // longest first: the problems still running at step k are a prefix
+    std::vector<BatchPlanEntry> order = plan;
+    std::stable_sort(order.begin(), order.end(),
+                     [](const BatchPlanEntry& a, const BatchPlanEntry& b) { return a.nsteps > b.nsteps; });
+
+    lsp::Ctl* ctl = (lsp::Ctl*)ws;
+    char* base = (char*)ws + lsp::kCtlBytes;
+    lsp::BatchProblem* d_table = (lsp::BatchProblem*)base;
+    base += round256((size_t)nprob * sizeof(lsp::BatchProblem));
+    int* d_block_prob = (int*)base;
+    base += round256((size_t)total_blocks * sizeof(int));
+
+    std::vector<lsp::BatchProblem> table(nprob);
+    std::vector<int> block_prob((size_t)total_blocks);
+    std::vector<int> prefix(nprob + 1, 0);
+    for (int j = 0; j < nprob; ++j) {
+        const BatchPlanEntry& e = order[j];
+        const lsp_grid* g = grids[e.p];
+        lsp::BatchProblem& P = table[j];
+        std::memset(&P, 0, sizeof(P));
+        P.a = base_args<float>(g, ctl);
+        P.a.tube = o->tube ? 1 : 0;
+        P.phi = (float*)phis[e.p];
+        P.target = o->tube ? (const float*)targets[e.p] : nullptr;
+        P.w1 = (float*)base;
+        base += e.field_bytes;
+        P.w2 = o->rk_order == 3 ? (float*)base : nullptr;
+        if (o->rk_order == 3) base += e.field_bytes;
+        P.dt = e.dt;
+        P.dt_last = e.dt_last;
+        P.nsteps = e.nsteps;
+        P.ndim = g->ndim;
+        P.dyn = g->dyn;
+        P.ch = e.ch;
+        P.nbx = e.nbx;
+        P.nby = e.nby;
+        P.nchunks = e.nchunks;
+        P.block_start = prefix[j];
+        P.nblocks = e.nblocks;
+        prefix[j + 1] = prefix[j] + e.nblocks;
+        for (int b = 0; b < e.nblocks; ++b) block_prob[(size_t)prefix[j] + b] = j;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // pageable sources: the copies are staged before the calls return
+    cudaError_t e = cudaMemcpyAsync(d_table, table.data(), table.size() * sizeof(table[0]),
+                                    cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(d_block_prob, block_prob.data(), block_prob.size() * sizeof(int),
+                                cudaMemcpyHostToDevice, st);
+    if (e) return cuda_fail(e, "upload batch table");
+
+    cudaStream_t es = st;
+    cudaStream_t cap = nullptr;
+    if (o->use_graph) {
+        if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) return cuda_fail(e, "create stream");
+        es = cap;
+        if ((e = cudaStreamBeginCapture(es, cudaStreamCaptureModeThreadLocal))) {
+            cudaStreamDestroy(cap);
+            return cuda_fail(e, "begin capture");
+        }
+    }
+    s = reset_flags(ws, es);
+    int nactive = nprob;
+    const int maxsteps = nprob ? order[0].nsteps : 0;
+    for (int k = 0; !s && k < maxsteps; ++k) {
+        while (nactive > 0 && order[nactive - 1].nsteps <= k) --nactive;
+        for (int stage = 0; stage < o->rk_order && !s; ++stage) {
+            e = lsp::launch_batched(o->scheme, d_table, d_block_prob, prefix[nactive], k, stage,
+                                    o->rk_order, es);
+            if (e) s = cuda_fail(e, "batched stage kernel");
+        }
+    }
+    if (o->use_graph) {
+        cudaGraph_t gr = nullptr;
+        e = cudaStreamEndCapture(es, &gr);
+        if (!s && e) s = cuda_fail(e, "end capture");
+        cudaGraphExec_t ex = nullptr;
+        if (!s && (e = cudaGraphInstantiate(&ex, gr, 0))) s = cuda_fail(e, "graph instantiate");
+        if (!s && (e = cudaGraphLaunch(ex, st))) s = cuda_fail(e, "graph launch");
+        if (ex) cudaGraphExecDestroy(ex);
+        if (gr) cudaGraphDestroy(gr);
+        cudaStreamDestroy(cap);
+    }
+    if (s) return s;
+    if (o->check_finite) return read_flags(ws, st);
+    return LSP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// ----------------------------------------------------------------- adjoint
+// Workspace of a checkpointed forward solve and its reverse sweep:
+// [ctl 256][W1][W2][acc 256][ckpt: C fields][seg: K fields][lam][lam_n]
+// [lam_a][lam_b][lam_v][contrib: 7*ndim fields], K = ceil(nsteps / C).
+struct AdjLayout {
+    int C, K;
+    size_t F;  // one field, rounded to 256 bytes
+    size_t off_acc, off_ckpt, off_seg, off_w1, off_w2, off_lam, off_lamn, off_lama, off_lamb,
+        off_lamv, off_contrib, total;
+};
+
+AdjLayout adj_layout(const lsp_grid* g, const lsp_solve_opts* o, int nsteps, int ncheck)
+{
+    AdjLayout L;
+    L.C = ncheck > 0 ? ncheck : (int)std::ceil(std::sqrt((double)std::max(nsteps, 1)));
+    if (L.C > nsteps) L.C = std::max(nsteps, 1);
+    L.K = (nsteps + L.C - 1) / L.C;
+    if (L.K < 1) L.K = 1;
+    L.F = round256((size_t)g->npts * elem_size(o->dtype));
+    // W1 and W2 come first so that the stage launches of a plain step (which
+    // expect [ctl][W1][W2]) can run on this workspace unchanged
+    size_t off = lsp::kCtlBytes;
+    L.off_w1 = off; off += L.F;
+    L.off_w2 = off; off += L.F;
+    L.off_acc = off; off += 256;
+    L.off_ckpt = off; off += (size_t)L.C * L.F;
+    L.off_seg = off; off += (size_t)L.K * L.F;
+    L.off_lam = off; off += L.F;
+    L.off_lamn = off; off += L.F;
+    L.off_lama = off; off += L.F;
+    L.off_lamb = off; off += L.F;
+    L.off_lamv = off; off += L.F;
+    L.off_contrib = off; off += (size_t)7 * g->ndim * L.F;
+    L.total = off;
+    return L;
+}
+
+lsp_status adj_check(const lsp_grid* g, const lsp_solve_opts* o, int nsteps)
+{
+    lsp_status s = check_opts(g, o);
+    if (s) return s;
+    if (!g->alpha_state) return fail(LSP_EUNSUPPORTED, "the adjoint needs state-only LF bounds");
+    if (g->dyn == LSP_DYN_QUADRATIC) return fail(LSP_EUNSUPPORTED, "no adjoint for QUADRATIC");
+    if (nsteps < 1) return fail(LSP_EINVAL, "nsteps must be >= 1");
+    return LSP_OK;
+}
+
+template <typename R>
+lsp_status adj_stage(const lsp_grid* g, const lsp_solve_opts* o, void* ws, const AdjLayout& Lo,
+                     const R* u, const R* phin, const R* target, const R* lam, R* lam_u, R* lam_n,
+                     R* lam_g, double dt, double c_n, double c_s, double c_l, bool tube,
+                     cudaStream_t st)
+{
+    lsp::AdjArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    a.u = u;
+    a.phin = phin;
+    a.target = target;
+    a.lam = lam;
+    a.lam_v = (R*)((char*)ws + Lo.off_lamv);
+    a.contrib = (R*)((char*)ws + Lo.off_contrib);
+    a.lam_u = lam_u;
+    a.lam_n = lam_n;
+    a.lam_g = tube ? lam_g : nullptr;
+    a.acc = (lsp::AdjAcc*)((char*)ws + Lo.off_acc);
+    long long sd = 1;
+    for (int k = g->ndim - 1; k >= 0; --k) {
+        a.n[k] = g->n[k];
+        a.stride[k] = (int)sd;
+        sd *= g->n[k];
+        a.periodic[k] = g->periodic[k];
+        a.inv_dx[k] = R(1.0 / g->dx[k]);
+        a.lo[k] = R(g->lo[k]);
+        a.h[k] = R(g->dx[k]);
+        a.alpha[k] = R(g->alpha[k]);
+    }
+    for (int i = 0; i < LSP_NPARAM; ++i) a.prm[i] = R(g->prm[i]);
+    a.dt = R(dt);
+    a.c_n = R(c_n);
+    a.c_s = R(c_s);
+    a.c_l = R(c_l);
+    a.tube = tube ? 1 : 0;
+    a.npts = (int)g->npts;
+    cudaError_t e = lsp::launch_adjoint_stage<R>(g->ndim, o->scheme, g->dyn, a, st);
+    return e ? cuda_fail(e, "adjoint stage kernels") : LSP_OK;
+}
+
+// d alpha_k / d prm_j at the node attaining alpha_k (FP64, host).
+void alpha_param_grads(const lsp_grid* g, const double* x, int k, double* gk)
+{
+    const double* c = g->prm;
+    for (int j = 0; j < LSP_NPARAM; ++j) gk[j] = 0.0;
+    auto sg = [](double v) { return v >= 0.0 ? 1.0 : -1.0; };
+    switch (g->dyn) {
+    case LSP_DYN_NORMAL_SPEED: gk[0] = 1.0; break;
+    case LSP_DYN_TRANSLATE: gk[k] = sg(c[k]); break;
+    case LSP_DYN_AIR3D:
+        if (k == 0) {
+            const double w = -c[0] + c[1] * std::cos(x[2]);
+            gk[0] = -sg(w);
+            gk[1] = sg(w) * std::cos(x[2]);
+            gk[2] = std::fabs(x[1]);
+        } else if (k == 1) {
+            gk[1] = std::fabs(std::sin(x[2]));
+            gk[2] = std::fabs(x[0]);
+        } else {
+            gk[2] = 1.0;
+            gk[3] = 1.0;
+        }
+        break;
+    case LSP_DYN_CAR4D:
+        if (k == 2) gk[0] = 1.0;
+        if (k == 3) gk[1] = 1.0;
+        break;
+    }
+}
+
+template <typename R>
+lsp_status adjoint_sweep(const lsp_grid* g, const lsp_solve_opts* o, const R* target, int nsteps,
+                         const R* lamT, R* lam0, R* lam_target, double* dprm, void* ws,
+                         const AdjLayout& Lo, cudaStream_t st)
+{
+    const size_t N = (size_t)g->npts;
+    const size_t NB = N * sizeof(R);
+    char* W = (char*)ws;
+    lsp::Ctl* ctl = (lsp::Ctl*)ws;
+    R* ckpt = (R*)(W + Lo.off_ckpt);
+    R* seg = (R*)(W + Lo.off_seg);
+    R* w1 = (R*)(W + Lo.off_w1);
+    R* w2 = (R*)(W + Lo.off_w2);
+    R* lam = (R*)(W + Lo.off_lam);
+    R* lamn = (R*)(W + Lo.off_lamn);
+    R* lama = (R*)(W + Lo.off_lama);
+    R* lamb = (R*)(W + Lo.off_lamb);
+    const size_t FE = Lo.F / sizeof(R);  // field stride in elements
+    const bool tube = o->tube != 0;
+    const int rk = o->rk_order;
+    const double dt = cfl_dt_host(g, o->cfl, 0.0, INFINITY);
+    cudaError_t e;
+    lsp_status s = LSP_OK;
+    if ((e = cudaMemsetAsync(W + Lo.off_acc, 0, 256, st))) return cuda_fail(e, "memset acc");
+    if ((e = cudaMemcpyAsync(lam, lamT, NB, cudaMemcpyDeviceToDevice, st))) return cuda_fail(e, "copy lamT");
+    if (lam_target && (e = cudaMemsetAsync(lam_target, 0, NB, st))) return cuda_fail(e, "memset lam_target");
+    for (int sg = (nsteps - 1) / Lo.K; sg >= 0 && !s; --sg) {
+        const int n0 = sg * Lo.K, n1 = std::min(n0 + Lo.K, nsteps);
+        // states phi^n, n0 <= n < n1, recomputed from the checkpoint
+        e = cudaMemcpyAsync(seg, ckpt + (size_t)sg * FE, NB, cudaMemcpyDeviceToDevice, st);
+        if (e) return cuda_fail(e, "restore checkpoint");
+        for (int n = n0; n + 1 < n1 && !s; ++n) {
+            R* nxt = seg + (size_t)(n - n0 + 1) * FE;
+            e = cudaMemcpyAsync(nxt, seg + (size_t)(n - n0) * FE, NB, cudaMemcpyDeviceToDevice, st);
+            if (e) return cuda_fail(e, "copy state");
+            s = enqueue_step<R>(g, o, nxt, target, dt, ws, st);
+        }
+        for (int n = n1 - 1; n >= n0 && !s; --n) {
+            const R* phin = seg + (size_t)(n - n0) * FE;
+            // the stage inputs of step n, recomputed bit for bit
+            if (rk >= 2) s = enqueue_stage<R>(g, o, ctl, phin, nullptr, nullptr, w1, dt, 0.0, 1.0, 1.0, false, st);
+            if (!s && rk == 3)
+                s = enqueue_stage<R>(g, o, ctl, w1, phin, nullptr, w2, dt, 0.75, 0.25, 0.25, false, st);
+            if (s) break;
+            if ((e = cudaMemsetAsync(lamn, 0, NB, st))) return cuda_fail(e, "memset");
+            if (rk == 1) {
+                // phi^{n+1} = [phi^n + dt L(phi^n)]_tube
+                s = adj_stage<R>(g, o, ws, Lo, phin, nullptr, target, lam, lamn, lamn, lam_target,
+                                 dt, 0.0, 1.0, 1.0, tube, st);
+            } else if (rk == 2) {
+                // phi^{n+1} = [1/2 phi^n + 1/2 W1 + 1/2 dt L(W1)]_tube
+                if ((e = cudaMemsetAsync(lama, 0, NB, st))) return cuda_fail(e, "memset");
+                s = adj_stage<R>(g, o, ws, Lo, w1, phin, target, lam, lama, lamn, lam_target, dt,
+                                 0.5, 0.5, 0.5, tube, st);
+                // W1 = phi^n + dt L(phi^n)
+                if (!s)
+                    s = adj_stage<R>(g, o, ws, Lo, phin, nullptr, nullptr, lama, lamn, lamn, nullptr,
+                                     dt, 0.0, 1.0, 1.0, false, st);
+            } else {
+                // phi^{n+1} = [1/3 phi^n + 2/3 W2 + 2/3 dt L(W2)]_tube
+                if ((e = cudaMemsetAsync(lamb, 0, NB, st))) return cuda_fail(e, "memset");
+                s = adj_stage<R>(g, o, ws, Lo, w2, phin, target, lam, lamb, lamn, lam_target, dt,
+                                 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, tube, st);
+                // W2 = 3/4 phi^n + 1/4 W1 + 1/4 dt L(W1)
+                if (!s && (e = cudaMemsetAsync(lama, 0, NB, st))) return cuda_fail(e, "memset");
+                if (!s)
+                    s = adj_stage<R>(g, o, ws, Lo, w1, phin, nullptr, lamb, lama, lamn, nullptr, dt,
+                                     0.75, 0.25, 0.25, false, st);
+                // W1 = phi^n + dt L(phi^n)
+                if (!s)
+                    s = adj_stage<R>(g, o, ws, Lo, phin, nullptr, nullptr, lama, lamn, lamn, nullptr,
+                                     dt, 0.0, 1.0, 1.0, false, st);
+            }
+            std::swap(lam, lamn);
+        }
+    }
+    if (s) return s;
+    if ((e = cudaMemcpyAsync(lam0, lam, NB, cudaMemcpyDeviceToDevice, st))) return cuda_fail(e, "copy lam0");
+    // parameters: direct (through H) + through alpha (dissipation and dt)
+    lsp::AdjAcc acc;
+    if ((e = cudaMemcpyAsync(&acc, W + Lo.off_acc, sizeof(acc), cudaMemcpyDeviceToHost, st)))
+        return cuda_fail(e, "read accumulators");
+    // the node attaining each alpha_k
+    lsp::GridGeom geo;
+    std::memset(&geo, 0, sizeof(geo));
+    geo.ndim = g->ndim;
+    geo.npts = g->npts;
+    for (int k = 0; k < g->ndim; ++k) {
+        geo.n[k] = g->n[k];
+        geo.lo[k] = g->lo[k];
+        geo.h[k] = g->dx[k];
+    }
+    for (int i = 0; i < LSP_NPARAM; ++i) geo.prm[i] = g->prm[i];
+    double* d_alpha = (double*)((char*)ctl->reserved);                       // 4 doubles
+    unsigned long long* d_arg = (unsigned long long*)((char*)ctl->reserved + 32);  // 4 indices
+    if ((e = cudaMemcpyAsync(d_alpha, g->alpha, 4 * sizeof(double), cudaMemcpyHostToDevice, st)))
+        return cuda_fail(e, "upload alpha");
+    if ((e = cudaMemsetAsync(d_arg, 0xff, 4 * sizeof(unsigned long long), st))) return cuda_fail(e, "memset");
+    if ((e = lsp::launch_alpha_argmax(g->dyn, geo, d_alpha, d_arg, st))) return cuda_fail(e, "argmax");
+    unsigned long long arg[4];
+    if ((e = cudaMemcpyAsync(arg, d_arg, sizeof(arg), cudaMemcpyDeviceToHost, st)))
+        return cuda_fail(e, "read argmax");
+    if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "synchronize");
+    double S = 0.0;
+    for (int k = 0; k < g->ndim; ++k) S += g->alpha[k] / g->dx[k];
+    for (int j = 0; j < LSP_NPARAM; ++j) dprm[j] = j < 4 ? acc.hprm[j] : 0.0;
+    for (int k = 0; k < g->ndim; ++k) {
+        double x[LSP_MAXD] = {0, 0, 0, 0};
+        long long r = (long long)arg[k];
+        for (int q = g->ndim - 1; q >= 0; --q) {
+            x[q] = g->lo[q] + (double)(r % g->n[q]) * g->dx[q];
+            r /= g->n[q];
+        }
+        double gk[LSP_NPARAM];
+        alpha_param_grads(g, x, k, gk);
+        const double dL_dalpha = acc.alpha[k] - acc.dt * o->cfl / (S * S * g->dx[k]);
+        for (int j = 0; j < LSP_NPARAM; ++j) dprm[j] += dL_dalpha * gk[j];
+    }
+    return LSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lsp_status lsp_adjoint_workspace_size(const lsp_grid* g, const lsp_solve_opts* o, int nsteps,
+                                      int ncheck, size_t* bytes)
+{
+    if (!bytes) return fail(LSP_EINVAL, "bytes is NULL");
+    lsp_status s = adj_check(g, o, nsteps);
+    if (s) return s;
+    *bytes = adj_layout(g, o, nsteps, ncheck).total;
+    return LSP_OK;
+}
+
+lsp_status lsp_hj_solve_ckpt(lsp_grid* g, const lsp_solve_opts* o, void* phi, const void* target,
+                             int nsteps, int ncheck, void* ws, size_t ws_size, void* stream)
+{
+    lsp_status s = adj_check(g, o, nsteps);
+    if (!s) s = check_field(phi, "phi");
+    if (!s && o->tube) s = check_field(target, "target");
+    if (s) return s;
+    if (!ws || !aligned16(ws)) return fail(LSP_EINVAL, "workspace must be non-NULL and 16-byte aligned");
+    const AdjLayout Lo = adj_layout(g, o, nsteps, ncheck);
+    if (ws_size < Lo.total) return fail(LSP_ENOMEM, "workspace has %zu bytes, needs %zu", ws_size, Lo.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    const double dt = cfl_dt_host(g, o->cfl, 0.0, INFINITY);
+    const size_t NB = (size_t)g->npts * elem_size(o->dtype);
+    if ((s = reset_flags(ws, st))) return s;
+    for (int n = 0; n < nsteps && !s; ++n) {
+        if (n % Lo.K == 0) {
+            cudaError_t e = cudaMemcpyAsync((char*)ws + Lo.off_ckpt + (size_t)(n / Lo.K) * Lo.F, phi,
+                                            NB, cudaMemcpyDeviceToDevice, st);
+            if (e) return cuda_fail(e, "store checkpoint");
+        }
+        s = step_any(g, o, phi, target, dt, ws, st);
+    }
+    if (s) return s;
+    if (o->check_finite) return read_flags(ws, st);
+    return LSP_OK;
+}
+
+lsp_status lsp_hj_adjoint(lsp_grid* g, const lsp_solve_opts* o, const void* target, int nsteps,
+                          int ncheck, const void* lamT, void* lam0, void* lam_target, double* dprm,
+                          void* ws, size_t ws_size, void* stream)
+{
+    lsp_status s = adj_check(g, o, nsteps);
+    if (!s) s = check_field(lamT, "lamT");
+    if (!s) s = check_field(lam0, "lam0");
+    if (!s && o->tube) s = check_field(target, "target");
+    if (!s && lam_target) s = check_field(lam_target, "lam_target");
+    if (s) return s;
+    if (!dprm) return fail(LSP_EINVAL, "dprm is NULL");
+    if (!ws || !aligned16(ws)) return fail(LSP_EINVAL, "workspace must be non-NULL and 16-byte aligned");
+    const AdjLayout Lo = adj_layout(g, o, nsteps, ncheck);
+    if (ws_size < Lo.total) return fail(LSP_ENOMEM, "workspace has %zu bytes, needs %zu", ws_size, Lo.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (o->dtype == LSP_F64)
+        return adjoint_sweep<double>(g, o, (const double*)target, nsteps, (const double*)lamT,
+                                     (double*)lam0, (double*)lam_target, dprm, ws, Lo, st);
+    return adjoint_sweep<float>(g, o, (const float*)target, nsteps, (const float*)lamT,
+                                (float*)lam0, (float*)lam_target, dprm, ws, Lo, st);
+}
+
+lsp_status lsp_loss_tube(const lsp_grid* g, int dtype, const void* phi, const void* queries,
+                         int nq, double* value_dev, void* grad, void* stream)
+{
+    if (!g) return fail(LSP_EINVAL, "grid is NULL");
+    lsp_status s = check_field(phi, "phi");
+    if (s) return s;
+    if (nq < 0 || (nq > 0 && !queries)) return fail(LSP_EINVAL, "bad queries");
+    if (!value_dev) return fail(LSP_EINVAL, "value_dev is NULL");
+    if (dtype != LSP_F32 && dtype != LSP_F64) return fail(LSP_EINVAL, "bad dtype");
+    cudaStream_t st = (cudaStream_t)stream;
+    double eps = 0.0, dV = 1.0;
+    for (int k = 0; k < g->ndim; ++k) {
+        eps = std::fmax(eps, g->dx[k]);
+        dV *= g->dx[k];
+    }
+    cudaError_t e = cudaMemsetAsync(value_dev, 0, sizeof(double), st);
+    if (!e && grad) e = cudaMemsetAsync(grad, 0, (size_t)g->npts * elem_size(dtype), st);
+    if (e) return cuda_fail(e, "memset");
+    auto fill = [&](auto& L) {
+        L.nq = nq;
+        L.ndim = g->ndim;
+        L.npts = (int)g->npts;
+        long long sd = 1;
+        for (int k = g->ndim - 1; k >= 0; --k) {
+            L.n[k] = g->n[k];
+            L.stride[k] = (int)sd;
+            sd *= g->n[k];
+            L.periodic[k] = g->periodic[k];
+            L.lo[k] = g->lo[k];
+            L.h[k] = g->dx[k];
+        }
+        L.inv_eps = 1.0 / eps;
+        L.dV = dV;
+    };
+    if (dtype == LSP_F64) {
+        lsp::LossArgs<double> L;
+        std::memset(&L, 0, sizeof(L));
+        L.phi = (const double*)phi;
+        L.queries = (const double*)queries;
+        fill(L);
+        e = lsp::launch_loss<double>(L, value_dev, (double*)grad, st);
+    } else {
+        lsp::LossArgs<float> L;
+        std::memset(&L, 0, sizeof(L));
+        L.phi = (const float*)phi;
+        L.queries = (const float*)queries;
+        fill(L);
+        e = lsp::launch_loss<float>(L, value_dev, (float*)grad, st);
+    }
+    return e ? cuda_fail(e, "loss kernels") : LSP_OK;
 }
 
 lsp_status lsp_check_status(const void* ws, void* stream)

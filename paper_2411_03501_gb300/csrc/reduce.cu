@@ -3,6 +3,8 @@
 // with partialFunc; alpha_k = max over the grid of the bound on |dH/dp_k|).
 #include "launch.h"
 #include "stage_generic.cuh"
+#include "stage_tiled.cuh"
+#include "adjoint.cuh"
 
 namespace lsp {
 
@@ -15,6 +17,45 @@ cudaError_t launch_alpha_state(int dyn, const GridGeom& g, unsigned long long* o
     case TRANSLATE: alpha_state_kernel<TRANSLATE><<<nb, 256, 0, s>>>(g, out); break;
     case AIR3D: alpha_state_kernel<AIR3D><<<nb, 256, 0, s>>>(g, out); break;
     case CAR4D: alpha_state_kernel<CAR4D><<<nb, 256, 0, s>>>(g, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+bool tile_valid(int ndim, int scheme, const Tile& t, const int* n)
+{
+    if (ndim != 3 && ndim != 4) return false;
+    const int G = ghost_width(scheme);
+    if (t.tb < 1 || t.ta < 1 || t.ch < 1 || t.tb * t.ta > 256) return false;
+    if (t.minb < 2 || t.minb > 4) return false;
+    // each thread stages at most 4 values of the haloed plane tile
+    if ((t.ta + 2 * G) * (t.tb + 2 * G) > 4 * t.ta * t.tb) return false;
+    const int nS = n[ndim - 3];
+    const long long nz = (long long)((nS + t.ch - 1) / t.ch) * (ndim == 4 ? n[0] : 1);
+    return nz <= 65535;
+}
+
+cudaError_t launch_stage_tiled(int ndim, int scheme, int dyn, const StageArgs<float>& a,
+                               const Tile& t, cudaStream_t s)
+{
+    switch (t.minb) {
+    case 2: return launch_stage_tiled_m<2>(ndim, scheme, dyn, a, t, s);
+    case 3: return launch_stage_tiled_m<3>(ndim, scheme, dyn, a, t, s);
+    case 4: return launch_stage_tiled_m<4>(ndim, scheme, dyn, a, t, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_alpha_argmax(int dyn, const GridGeom& g, const double* alpha,
+                                unsigned long long* out, cudaStream_t s)
+{
+    long long b = (g.npts + 255) / 256;
+    const int nb = (int)(b < 152 * 8 ? (b < 1 ? 1 : b) : 152 * 8);
+    switch (dyn) {
+    case NORMAL_SPEED: alpha_argmax_kernel<NORMAL_SPEED><<<nb, 256, 0, s>>>(g, alpha, out); break;
+    case TRANSLATE: alpha_argmax_kernel<TRANSLATE><<<nb, 256, 0, s>>>(g, alpha, out); break;
+    case AIR3D: alpha_argmax_kernel<AIR3D><<<nb, 256, 0, s>>>(g, alpha, out); break;
+    case CAR4D: alpha_argmax_kernel<CAR4D><<<nb, 256, 0, s>>>(g, alpha, out); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

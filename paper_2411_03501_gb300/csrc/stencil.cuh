@@ -190,6 +190,25 @@ __device__ __forceinline__ R hamiltonian(const R* x, const R* p, const R* prm)
     }
 }
 
+// Hamiltonian with the coordinate-only factors (sin/cos of the heading)
+// precomputed by the caller: hamiltonian_sc(x, p, prm, sin th, cos th).
+template <int DYN, int NDIM, typename R>
+__device__ __forceinline__ R hamiltonian_sc(const R* x, const R* p, const R* prm, R s, R c)
+{
+    if constexpr (DYN == AIR3D) {
+        const R ve = prm[0], vp = prm[1], um = prm[2], dm = prm[3];
+        const R v = p[0] * (-ve + vp * c) + p[1] * (vp * s) +
+                    um * rabs(p[0] * x[1] - p[1] * x[0] - p[2]) - dm * rabs(p[2]);
+        return -v;
+    } else if constexpr (DYN == CAR4D) {
+        const R v = x[3];
+        const R m = p[0] * v * c + p[1] * v * s - prm[0] * rabs(p[2]) - prm[1] * rabs(p[3]);
+        return -m;
+    } else {
+        return hamiltonian<DYN, NDIM>(x, p, prm);
+    }
+}
+
 // Per-node bound on |dH/dp_k| for state-only bounds (FP64, used once per
 // grid by the reduction that yields the global-LF coefficients).
 template <int DYN>

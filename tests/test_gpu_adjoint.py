@@ -1,0 +1,178 @@
+"""The discrete adjoint on the GPU (through the C ABI) against the FP64
+oracle's adjoint, against central finite differences of the GPU forward
+map, across checkpoint counts, and through the autograd wrapper."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_helpers import rounded, to_dev
+from paper_2411_03501_gb300 import binding as B
+from paper_2411_03501_gb300 import workloads as W
+from paper_2411_03501_gb300.autograd import HJTube
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(kind, scheme, dtype, rk=3):
+    if kind == "air3d":
+        spec = W.air3d(nx=[13, 12, 14], scheme=scheme, ve=4.0, vp=5.5, we=1.1, wp=0.9,
+                       dtype=dtype, rk=rk)[0]
+        nsteps = 4
+    elif kind == "car4d":
+        spec = W.car4d(n=8, scheme=scheme, dtype=dtype)[0]
+        spec["n"] = [9, 8, 9, 8]
+        nsteps = 3
+    else:
+        spec = W.problem(2, [17, 15], [-1, -1], [1, 1], [False, True], scheme, "normal_speed",
+                         [1.3], rk=rk, cfl=0.75, tube=True, dtype=dtype)
+        nsteps = 5
+    phi0 = W.smooth_field(spec, seed=21) + 0.5 * W.circle_sdf(
+        spec, 0.4 * (spec["hi"][0] - spec["lo"][0]) / 2)
+    g = phi0 + 0.2 + 0.3 * W.smooth_field(spec, seed=22)
+    return spec, rounded(phi0, dtype), rounded(g, dtype), nsteps
+
+
+def _gpu_adjoint(spec, phi0, g, nsteps, lamT, ncheck=0):
+    P = B.Problem(spec)
+    nbytes = B.lsp_adjoint_workspace_size(P.grid, P.opts, nsteps, ncheck)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    dt = spec["dtype"]
+    phi = to_dev(phi0, dt)
+    gt = to_dev(g, dt)
+    B.lsp_hj_solve_ckpt(P.grid, P.opts, phi, gt, nsteps, ncheck, ws)
+    lam0 = torch.empty_like(phi)
+    lamg = torch.empty_like(phi)
+    dprm = B.lsp_hj_adjoint(P.grid, P.opts, gt, nsteps, ncheck, to_dev(lamT, dt), lam0, lamg, ws)
+    torch.cuda.synchronize()
+    c = lambda t: t.double().cpu().numpy()  # noqa: E731
+    return c(phi), c(lam0), c(lamg), np.array(dprm)
+
+
+CASES = [("air3d", "weno5", 3), ("air3d", "eno3", 3), ("air3d", "eno2", 2),
+         ("air3d", "upwind1", 1), ("car4d", "eno3", 3), ("normal2d", "weno5", 3)]
+
+
+@pytest.mark.parametrize("kind,scheme,rk", CASES)
+def test_fp64_adjoint_matches_oracle(kind, scheme, rk):
+    """FP64 GPU adjoint (JP-form WENO gradient, two-pass gather) against the
+    oracle's hand-written reverse (paper-form WENO gradient): the same
+    derivative up to rounding."""
+    spec, phi0, g, nsteps = _case(kind, scheme, "f64", rk)
+    lamT = np.random.default_rng(3).standard_normal(spec["n"])
+    phiT, lam0, lamg, dprm = _gpu_adjoint(spec, phi0, g, nsteps, lamT)
+    o0, og, oprm, ophiT = oracle.adjoint(spec, phi0, nsteps, rk, spec["cfl"], lamT, target=g)
+    assert np.abs(phiT - ophiT).max() <= 1e-11 * np.abs(ophiT).max()
+    assert np.abs(lam0 - o0).max() <= 1e-9 * np.abs(o0).max(), np.abs(lam0 - o0).max()
+    assert np.abs(lamg - og).max() <= 1e-9 * max(np.abs(og).max(), 1e-300)
+    npar = len(spec["params"])
+    np.testing.assert_allclose(dprm[:npar], oprm[:npar], rtol=1e-8, atol=1e-9 * np.abs(oprm).max())
+
+
+@pytest.mark.parametrize("kind,scheme,rk", CASES[:2] + CASES[4:])
+def test_fp32_adjoint_matches_oracle(kind, scheme, rk):
+    spec, phi0, g, nsteps = _case(kind, scheme, "f32", rk)
+    lamT = rounded(np.random.default_rng(4).standard_normal(spec["n"]), "f32")
+    _, lam0, lamg, dprm = _gpu_adjoint(spec, phi0, g, nsteps, lamT)
+    o0, og, oprm, _ = oracle.adjoint(spec, phi0, nsteps, rk, spec["cfl"], lamT, target=g)
+    assert np.abs(lam0 - o0).max() <= 1e-4 * np.abs(o0).max(), np.abs(lam0 - o0).max()
+    assert np.abs(lamg - og).max() <= 1e-4 * max(np.abs(og).max(), 1e-30)
+    npar = len(spec["params"])
+    np.testing.assert_allclose(dprm[:npar], oprm[:npar], rtol=1e-3, atol=1e-4 * np.abs(oprm).max())
+
+
+def test_checkpoint_counts_agree():
+    """sqrt(N) checkpointing recomputes the same states: any checkpoint
+    count gives the same gradient (up to the order of the FP64 parameter
+    sums and of the boundary folds)."""
+    spec, phi0, g, _ = _case("air3d", "weno5", "f64")
+    nsteps = 9
+    lamT = np.random.default_rng(5).standard_normal(spec["n"])
+    ref = _gpu_adjoint(spec, phi0, g, nsteps, lamT, ncheck=0)
+    for nc in (1, 2, 9):
+        got = _gpu_adjoint(spec, phi0, g, nsteps, lamT, ncheck=nc)
+        assert np.abs(got[1] - ref[1]).max() <= 1e-12 * np.abs(ref[1]).max()
+        np.testing.assert_allclose(got[3], ref[3], rtol=1e-12, atol=1e-14)
+
+
+def _air3d_adjoint_problem(n, nsteps, dtype, radius=5.0):
+    spec = W.air3d(n=n, dtype=dtype)[0]
+    sdf = W.circle_sdf(spec, 0.0)  # distance to the cylinder axis
+    rng = np.random.default_rng(20241106)
+    q = np.stack([rng.uniform(spec["lo"][k], spec["hi"][k], 1024) for k in range(3)], 1)
+    return spec, sdf, q
+
+
+def _loss_of(tube, sdf_t, q_t, r, params):
+    target = sdf_t - r
+    phiT = tube(target, target, params)
+    return tube.loss(phiT, q_t)
+
+
+def test_autograd_matches_central_differences_fp64():
+    """dLoss/d(v_e, v_p, turn bounds, target radius) through the autograd
+    wrapper (FP64) against central differences of the same forward map."""
+    spec, sdf, q = _air3d_adjoint_problem(21, 12, "f64")
+    tube = HJTube(spec, nsteps=12)
+    sdf_t = torch.as_tensor(sdf, device="cuda")
+    q_t = torch.as_tensor(q, device="cuda")
+    params = torch.tensor(spec["params"], dtype=torch.float64, requires_grad=True)
+    r = torch.tensor(5.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    L = _loss_of(tube, sdf_t, q_t, r, params)
+    L.backward()
+    h = 1e-6
+    with torch.no_grad():
+        for j in range(4):
+            pp = params.detach().clone()
+            pm = params.detach().clone()
+            pp[j] += h
+            pm[j] -= h
+            fd = (_loss_of(tube, sdf_t, q_t, r, pp) - _loss_of(tube, sdf_t, q_t, r, pm)).item() / (2 * h)
+            assert abs(fd - params.grad[j].item()) <= 1e-5 * (abs(fd) + 1e-3), (j, fd, params.grad[j])
+        fd = (_loss_of(tube, sdf_t, q_t, r + h, params) - _loss_of(tube, sdf_t, q_t, r - h, params)).item() / (2 * h)
+        assert abs(fd - r.grad.item()) <= 1e-5 * (abs(fd) + 1e-3), (fd, r.grad)
+
+
+@pytest.mark.slow
+def test_adjoint_workload_fp32_against_fd_and_fp64():
+    """The differentiation workload: air3d tube at 129^3, 200 RK3 steps, FP32,
+    loss = smoothed volume + values at 1024 seeded query states.  Gradients
+    with respect to v_e, v_p, the shared turn-rate bound and the target
+    radius: against central differences (h = 1e-3) of the FP32 forward, and
+    against the FP64 adjoint of the same solve."""
+    n, nsteps = 129, 200
+    res = {}
+    for dtype in ("f32", "f64"):
+        spec, sdf, q = _air3d_adjoint_problem(n, nsteps, dtype)
+        tube = HJTube(spec, nsteps=nsteps)
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        sdf_t = torch.as_tensor(sdf, device="cuda").to(tdt)
+        q_t = torch.as_tensor(q, device="cuda").to(tdt)
+        # the shared turn-rate bound w enters as (v_e, v_p, w, w)
+        base = torch.tensor([5.0, 5.0, 1.0], dtype=torch.float64, requires_grad=True)
+        r = torch.tensor(5.0, dtype=torch.float64, requires_grad=True)
+
+        def run(b, rr):
+            params = torch.stack([b[0], b[1], b[2], b[2]])
+            target = sdf_t - rr.to("cuda").to(tdt)
+            return tube.loss(tube(target, target, params), q_t)
+
+        L = run(base, r)
+        L.backward()
+        res[dtype] = (L.item(), base.grad.numpy().copy(), r.grad.item())
+        if dtype == "f32":
+            h = 1e-3
+            with torch.no_grad():
+                for j in range(3):
+                    bp = base.detach().clone()
+                    bm = base.detach().clone()
+                    bp[j] += h
+                    bm[j] -= h
+                    fd = (run(bp, r) - run(bm, r)).item() / (2 * h)
+                    g = res["f32"][1][j]
+                    assert abs(fd - g) <= 2e-2 * abs(fd) + 1e-2, (j, fd, g)
+                fd = (run(base, r + h) - run(base, r - h)).item() / (2 * h)
+                assert abs(fd - res["f32"][2]) <= 2e-2 * abs(fd) + 1e-2, (fd, res["f32"][2])
+    g32, g64 = res["f32"], res["f64"]
+    np.testing.assert_allclose(g32[1], g64[1], rtol=1e-2, atol=1e-3 * np.abs(g64[1]).max())
+    assert abs(g32[2] - g64[2]) <= 1e-2 * abs(g64[2]) + 1e-3

@@ -28,3 +28,35 @@ def test_extrapolated_boundary_layer_amplifies_rounding(orc):
     assert d[inner].max() < 1e-4 * scale
     assert d.max() > 1e-4 * scale  # the layer is worse than the bar ...
     assert d.max() < 3e-3 * scale  # ... and within the bound the GPU tests use
+
+
+@pytest.mark.slow
+def test_symmetric_valley_amplifies_asymmetric_perturbations(orc):
+    """An air3d tube is symmetric under (x, y, theta) -> (x, -y, -theta); on
+    the plane theta = 0 the value has a valley at y = 0 whose symmetric state
+    the discrete scheme does not hold against asymmetric perturbations.
+    Rounding the field to FP32 each step keeps the symmetry (equal values
+    round alike) and moves the solution by ~1e-7 max|phi|; a random relative
+    perturbation of 1e-7 of the initial field alone moves it by ~3e-4 max|phi|
+    there.  FP32 arithmetic is such a perturbation, which is why whole-solve
+    FP32 bars are set against the oracle's own spread under FP32-sized
+    noise."""
+    sp, p0, g = W.batched(count=6, seed=7, scale=0.3)[4]  # air3d 34^3, speed 3.11
+    p0 = p0.astype(np.float32).astype(np.float64)
+    g = g.astype(np.float32).astype(np.float64)
+    ref, st = orc.solve(sp, p0, sp["t_final"], 3, 0.75, target=g)
+    scale = np.abs(ref).max()
+    a = orc.alpha(sp, p0)
+    p, t = p0.copy(), 0.0
+    for _ in range(st["steps"]):
+        dt = orc.cfl_dt(sp, a, 0.75, t, sp["t_final"])
+        p = orc.step(sp, p, dt, 3, target=g).astype(np.float32).astype(np.float64)
+        t += dt
+    assert np.abs(p - ref).max() < 1e-5 * scale
+    rng = np.random.default_rng(1)
+    b, _ = orc.solve(sp, p0 * (1 + 1e-7 * rng.standard_normal(p0.shape)), sp["t_final"], 3, 0.75,
+                     target=g)
+    d = np.abs(b - ref)
+    assert d.max() > 1e-4 * scale
+    i = np.unravel_index(d.argmax(), d.shape)
+    assert i[2] == 0 and abs(i[1] - (sp["n"][1] - 1) / 2) < 2  # theta = 0, y ~ 0

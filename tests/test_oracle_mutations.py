@@ -1,6 +1,9 @@
 """The oracle's pins are discriminating: each plausible mistake planted in a
 copy of the oracle source (a flipped sign, a wrong index or coefficient, a
-swapped operand) makes at least one pin in test_oracle_pins.py fail.
+swapped operand) makes at least one pin fail -- test_oracle_pins.py for the
+forward scheme, test_oracle_adjoint.py for the discrete adjoint.  The first
+occurrence of each anchor is mutated (the forward code precedes the adjoint
+code that mirrors some of its lines).
 
 Mistakes are planted only in a temporary copy of the C oracle, compiled on
 the CPU; the committed oracle is untouched.
@@ -57,22 +60,43 @@ MUTANTS = {
                          "if (k == 1) return fabs(x[3] * cos(x[2]));"),
 }
 
+# mistakes in the discrete adjoint, caught by the finite-difference pins
+ADJOINT_MUTANTS = {
+    "adj_weno_eps_term": ("if (m == mstar) gm -= bsum * 2e-6 * v[mstar];",
+                          "if (m == mstar) gm += bsum * 2e-6 * v[mstar];"),
+    "adj_weno_sigma_factor": ("double ds = 13.0 / 6.0 * a[k] * da[k][m] + 0.5 * b[k] * db[k][m];",
+                              "double ds = 13.0 / 12.0 * a[k] * da[k][m] + 0.5 * b[k] * db[k][m];"),
+    "adj_eno_q2_coeff": ("c[(j - 1) - i + 3] += f2;", "c[(j - 1) - i + 3] -= f2;"),
+    "adj_air3d_dHdp2": ("hp[1] = -(vp * sin(th) - um * g1 * X);",
+                        "hp[1] = -(vp * sin(th) + um * g1 * X);"),
+    "adj_alpha_dt_path": ("double dL_dalpha = alpha_acc[k] - dt_acc * cfl / (S * S * orc_dx(P, k));",
+                          "double dL_dalpha = alpha_acc[k] + dt_acc * cfl / (S * S * orc_dx(P, k));"),
+    "adj_ghost_weight": ("wt[0] = 1.0 + k;\n        node[1] = 1;",
+                         "wt[0] = 1.0 - k;\n        node[1] = 1;"),
+    "adj_tube_branch": ("if (g && g[i] < v) { /* the min took the target */",
+                        "if (g && g[i] > v) { /* the min took the target */"),
+    "adj_rk3_stage2_weight": ("ln[i] += 0.75 * lb[i];", "ln[i] += 0.25 * lb[i];"),
+}
+
 
 @pytest.mark.slow
 @pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
-@pytest.mark.parametrize("name", sorted(MUTANTS))
+@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(ADJOINT_MUTANTS))
 def test_planted_mistake_is_caught(tmp_path, name):
     src = open(SRC).read()
-    old, new = MUTANTS[name]
-    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    adjoint = name in ADJOINT_MUTANTS
+    old, new = (ADJOINT_MUTANTS if adjoint else MUTANTS)[name]
+    old, new = old.replace("\\n", "\n"), new.replace("\\n", "\n")
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
     c = tmp_path / "mutant.c"
-    c.write_text(src.replace(old, new))
+    c.write_text(src.replace(old, new, 1))
     so = tmp_path / "mutant.so"
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", str(c), "-o", str(so), "-lm"],
                    check=True)
     r = subprocess.run(
-        [sys.executable, "-m", "pytest", os.path.join(HERE, "test_oracle_pins.py"), "-x", "-q",
-         "-p", "no:cacheprovider"],
+        [sys.executable, "-m", "pytest",
+         os.path.join(HERE, "test_oracle_adjoint.py" if adjoint else "test_oracle_pins.py"), "-x",
+         "-q", "-p", "no:cacheprovider"],
         env=dict(os.environ, LSP_ORACLE_LIB=str(so)), capture_output=True, text=True,
         timeout=600)
     assert r.returncode != 0, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"

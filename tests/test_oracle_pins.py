@@ -184,14 +184,19 @@ def test_derivative_is_homogeneous(orc, scheme):
 
 
 def test_eno_tie_margin_reported(orc):
-    """The selection margin is 0 at an exact tie and 1 where no choice is
-    made (non-ENO schemes)."""
+    """The selection margin is 0 at an exact tie between candidates of
+    opposite sign (a step: second differences +1 and -1), 1 where the
+    candidates agree in sign (a parabola: equal second differences) and 1
+    where no choice is made (non-ENO schemes)."""
     spec = _spec1d(9, "eno2")
-    phi = np.array([0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 1.0, 0.0, 0.0])
-    _, _, tie = orc.derivs(spec, phi, 0, with_ties=True)
+    step = np.array([0.0, 0.0, 0.0, 0.0, 1.0, 1.0, 1.0, 1.0, 1.0])
+    _, _, tie = orc.derivs(spec, step, 0, with_ties=True)
     assert tie.min() == 0.0
+    x = W.axis_nodes(spec, 0)
+    _, _, tie = orc.derivs(spec, x ** 2, 0, with_ties=True)
+    assert np.all(tie == 1.0)
     spec = _spec1d(9, "weno5")
-    _, _, tie = orc.derivs(spec, phi, 0, with_ties=True)
+    _, _, tie = orc.derivs(spec, step, 0, with_ties=True)
     assert np.all(tie == 1.0)
 
 
