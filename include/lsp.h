@@ -211,6 +211,31 @@ lsp_status lsp_autotune(lsp_grid* grid, const lsp_solve_opts* opts, const void* 
                         void* workspace, size_t workspace_bytes, void* stream, int* tb, int* ta,
                         int* ch, int* minb);
 
+/* lsp_hj_solve without a workspace argument, for callers that cannot
+ * allocate device memory: for example a real-time control loop that must
+ * not call cudaMalloc/cudaFree (they can block and synchronise the whole
+ * device), or a host whose device memory is entirely owned by another
+ * allocator (a framework's caching allocator, a fixed arena) and so has no
+ * buffer to hand over.  The paper has no counterpart: this is a property of
+ * the library, not of the method.
+ *  - Scratch lives in a static 32 MiB device array inside the library (held
+ *    on every GPU that loads the library until the process exits); grids
+ *    whose lsp_workspace_size exceeds 32 MiB are rejected with LSP_ENOMEM
+ *    and a message giving both sizes (FP32 RK3: up to ~4.19M nodes).
+ *  - The first call on a device looks up the array's device address (a
+ *    one-time set-up with that device current); make that first call before
+ *    any stream capture.
+ *  - Every call shares the one array, which keeps the last call's contents
+ *    (the solve never reads them: flags are cleared on entry and stage
+ *    fields are written before being read).  Calls whose GPU work overlaps
+ *    (different streams, threads or processes on the same device) race on
+ *    it: serialise them.
+ *  - opts->use_graph must be 0.  Other arguments, results and errors as for
+ *    lsp_hj_solve.  Nothing is allocated. */
+lsp_status lsp_hj_solve_noalloc(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
+                                const void* target, double t0, double t_final,
+                                lsp_solve_stats* stats, void* stream);
+
 /* Batched solves: nprob independent problems (own grid, dynamics, CFL step
  * and t_final each) advanced together, problem i from t = 0 to t_final[i].
  * One kernel launch advances one RK stage of every problem that still has

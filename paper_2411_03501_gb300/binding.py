@@ -24,7 +24,7 @@ DTYPES = {"f32": 0, "f64": 1}
 EXPORTS = [
     "lsp_version", "lsp_status_string", "lsp_last_error", "lsp_grid_create", "lsp_grid_destroy",
     "lsp_set_dynamics", "lsp_get_alpha", "lsp_workspace_size", "lsp_cfl_dt", "lsp_hj_rate",
-    "lsp_hj_step", "lsp_hj_solve", "lsp_check_status",
+    "lsp_hj_step", "lsp_hj_solve", "lsp_check_status", "lsp_hj_solve_noalloc",
     "lsp_set_tile", "lsp_get_tile", "lsp_autotune", "lsp_batched_workspace_size",
     "lsp_hj_solve_batched", "lsp_adjoint_workspace_size", "lsp_hj_solve_ckpt", "lsp_hj_adjoint",
     "lsp_loss_tube",
@@ -94,6 +94,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.lsp_hj_solve.argtypes = [vp, op, vp, vp, ctypes.c_double, ctypes.c_double, vp, sz,
                                ctypes.POINTER(lsp_solve_stats), vp]
     L.lsp_check_status.argtypes = [vp, vp]
+    L.lsp_hj_solve_noalloc.argtypes = [vp, op, vp, vp, ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(lsp_solve_stats), vp]
     ip = ctypes.POINTER(ctypes.c_int)
     L.lsp_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.lsp_get_tile.argtypes = [vp, op, ip, ip, ip, ip]
@@ -112,7 +114,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
                  "lsp_hj_adjoint", "lsp_loss_tube"):
         getattr(L, name).restype = ctypes.c_int
     for name in ("lsp_grid_create", "lsp_set_dynamics", "lsp_get_alpha", "lsp_workspace_size",
-                 "lsp_cfl_dt", "lsp_hj_rate", "lsp_hj_step", "lsp_hj_solve", "lsp_check_status"):
+                 "lsp_cfl_dt", "lsp_hj_rate", "lsp_hj_step", "lsp_hj_solve", "lsp_check_status",
+                 "lsp_hj_solve_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -221,6 +224,15 @@ def lsp_hj_solve(grid: Grid, opts, phi, target, t0, t_final, workspace, stream=N
                                _stream(stream)))
     return {"steps": st.steps, "stages": st.stages, "dt_min": st.dt_min, "dt_max": st.dt_max,
             "t_end": st.t_end}
+
+
+def lsp_hj_solve_noalloc(grid: Grid, opts, phi, target, t0, t_final, stream=None) -> dict:
+    st = lsp_solve_stats()
+    _check(load().lsp_hj_solve_noalloc(grid.handle, ctypes.byref(opts), _ptr(phi), _ptr(target),
+                                       t0, t_final, ctypes.byref(st), _stream(stream)))
+    return {"steps": st.steps, "stages": st.stages, "dt_min": st.dt_min, "dt_max": st.dt_max,
+            "t_end": st.t_end}
+
 
 
 def lsp_set_tile(grid: Grid, tb: int, ta: int, ch: int, minb: int = 3):

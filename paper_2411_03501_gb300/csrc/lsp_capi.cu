@@ -307,6 +307,14 @@ lsp_status check_field(const void* p, const char* name)
 
 }  // namespace
 
+namespace lsp {
+// Record the thread's last-error text from another translation unit.
+void set_last_error(const char* msg)
+{
+    std::snprintf(g_err, sizeof(g_err), "%s", msg);
+}
+}  // namespace lsp
+
 extern "C" {
 
 int lsp_version(void) { return 100; }
