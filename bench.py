@@ -89,6 +89,37 @@ def algorithmic(spec) -> tuple[float, float]:
     return words * word, float(flops)
 
 
+KERNEL_SOURCES = ["stencil.cuh", "stage_tiled.cuh", "stage_tiled.inl", "stage_generic.cuh"]
+
+
+def kernel_hash() -> str:
+    """Hash of the stage-kernel sources: a DRAM-traffic figure taken by ncu is
+    reported only while the kernel it was measured on is unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2411_03501_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload_name: str):
+    """dram__bytes_read.sum + dram__bytes_write.sum per stage launch from the
+    committed ncu summary of this workload (profiles/*.md lines
+    `traffic_bytes_per_launch[<workload>]: <bytes> kernel_hash=<hash>`), or
+    None when no summary matches the current kernel sources."""
+    import glob
+    want = kernel_hash()
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for ln in open(f):
+            tag = f"traffic_bytes_per_launch[{workload_name}]:"
+            if ln.strip().startswith(tag):
+                parts = ln.strip()[len(tag):].split()
+                if len(parts) >= 2 and parts[1] == f"kernel_hash={want}":
+                    return float(parts[0])
+    return None
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) during the timed region."""
 
@@ -198,7 +229,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     P = B.Problem(spec, use_graph=args.graph)
     tdt = P.torch_dtype
     phi0_d = torch.as_tensor(phi0).to("cuda", tdt).contiguous()
-    tile = P.autotune(phi0_d) if args.autotune else P.tile()
+    if args.tile:
+        P.set_tile(*[int(v) for v in args.tile.split(",")])
+        tile = P.tile()
+    else:
+        tile = P.autotune(phi0_d) if args.autotune else P.tile()
     g_d = torch.as_tensor(g).to("cuda", tdt).contiguous() if g is not None else None
     phi = torch.empty_like(phi0_d)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -299,11 +334,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes, TFLOP/s
     hbm_peak = float(peaks["hbm_gbs"])
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", f"traffic_{spec['name']}.json")
-    if os.path.exists(tfile):
-        with open(tfile) as f:
-            traffic = json.load(f).get("bytes_per_launch")
+    traffic = measured_traffic(spec["name"])
     alu = {"bound": "alu", "achieved": flop_ach, "peak": alu_peak, "unit": "TFLOP/s",
            "frac": flop_ach / alu_peak, "traffic": traffic,
            "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock"}
@@ -469,6 +500,125 @@ def run_batched(args, rank: int, world: int, local_rank: int):
     return 0
 
 
+def run_adjoint(args, rank: int, world: int, local_rank: int):
+    """The differentiation workload: the air3d tube at 129^3 in FP32 over 200
+    fixed RK3 steps; loss = smoothed volume of {phi <= 0} + phi at 1024 seeded
+    query states.  One benchmark step = forward solve with sqrt(N) checkpoints,
+    loss, reverse sweep: gradients with respect to v_e, v_p, the shared
+    turn-rate bound, the target radius (and phi0 = target).  The metric counts
+    the forward's point-stages per second of the whole gradient evaluation;
+    the plain forward (same 200 steps) is timed beside it.  Replicas under
+    torchrun."""
+    import numpy as np
+    import torch
+
+    from paper_2411_03501_gb300 import build as BLD
+    from paper_2411_03501_gb300 import workloads as W
+    from paper_2411_03501_gb300.autograd import HJTube
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0 or not os.path.exists(BLD.LIB):
+        BLD.build()
+    if world > 1:
+        torch.distributed.barrier()
+    n, nsteps = 129, 200
+    spec = W.air3d(n=n)[0]
+    npts = n ** 3
+    h_sdf = torch.as_tensor(W.circle_sdf(spec, 0.0), dtype=torch.float32).pin_memory()
+    rng = np.random.default_rng(20241106)
+    h_q = torch.as_tensor(np.stack([rng.uniform(spec["lo"][k], spec["hi"][k], 1024)
+                                    for k in range(3)], 1), dtype=torch.float32).pin_memory()
+    sdf, q = h_sdf.cuda(), h_q.cuda()
+    tube = HJTube(spec, nsteps=nsteps)
+    stream = torch.cuda.current_stream()
+
+    def grad_step(sdf_d, q_d):
+        base = torch.tensor([5.0, 5.0, 1.0], dtype=torch.float64, requires_grad=True)
+        r = torch.tensor(5.0, dtype=torch.float64, requires_grad=True)
+        params = torch.stack([base[0], base[1], base[2], base[2]])
+        target = sdf_d - r.to("cuda").float()
+        loss = tube.loss(tube(target, target, params), q_d)
+        loss.backward()
+        return torch.cat([base.grad, r.grad.reshape(1)])
+
+    for _ in range(args.warmup):
+        g = grad_step(sdf, q)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clk = ClockSampler(local_rank, os.path.join(args.outdir, f"clocks_rank{rank}.csv"))
+    if world > 1:
+        torch.distributed.barrier()
+    with clk:
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            g = grad_step(sdf, q)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    # plain forward of the same 200 steps (one checkpoint: a single copy)
+    plain = HJTube(spec, nsteps=nsteps, ncheck=1)
+    params = torch.tensor(spec["params"], dtype=torch.float64)
+    tgt = sdf - 5.0
+    with torch.no_grad():
+        for _ in range(2):
+            plain(tgt, tgt, params)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            plain(tgt, tgt, params)
+        f1.record(stream)
+        torch.cuda.synchronize()
+    fwd_ms = f0.elapsed_time(f1)
+    # end to end: the SDF and queries from pinned host memory, gradients back
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g = grad_step(h_sdf.cuda(non_blocking=True), h_q.cuda(non_blocking=True)).cpu()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = torch.tensor([ms, e0.elapsed_time(e1), fwd_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms, e2e_ms, fwd_ms = (float(v) for v in t.tolist())
+    units = world * npts * nsteps * 3 * args.steps
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "adjoint_air3d_129^3_200xrk3_f32", "points": npts,
+                   "rk_steps": nsteps, "checkpoints": tube.ncheck or int(np.ceil(np.sqrt(nsteps))),
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "fields (8.6 MB each) partly L2-resident; no flush",
+                   "plain_forward_value": units / (fwd_ms / 1e3),
+                   "gradient_over_forward_time": ms / fwd_ms,
+                   "grads[v_e, v_p, w, r]": [float(v) for v in g.tolist()]},
+        "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": h_sdf.numel() * 4 + h_q.numel() * 4,
+                "d2h_bytes_per_step": 4 * 8},
+        "gpu_launches": adjoint_launches(nsteps, 3) * args.steps, "roofline": None,
+        "cpu_baseline": None, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def adjoint_launches(nsteps: int, rk: int) -> int:
+    """Kernels of one gradient evaluation: forward stages, the segment
+    recomputation from sqrt(N) checkpoints, the per-step recomputation of the
+    stage inputs, two adjoint kernels per stage, the GLF argmax, two loss
+    kernels."""
+    import math
+    C = math.ceil(math.sqrt(nsteps))
+    K = math.ceil(nsteps / C)
+    nseg = math.ceil(nsteps / K)
+    return (nsteps * rk + (nsteps - nseg) * rk + nsteps * (rk - 1) + 2 * rk * nsteps + 1 + 2)
+
+
 def run_steps(args):
     """Profiling mode: `warmup` then `steps` single RK steps of the workload
     (3 stage launches each for RK3), timed with events; for ncu captures."""
@@ -482,7 +632,11 @@ def run_steps(args):
     P = B.Problem(spec)
     phi = torch.as_tensor(phi0).to("cuda", P.torch_dtype).contiguous()
     gd = torch.as_tensor(g).to("cuda", P.torch_dtype).contiguous() if g is not None else None
-    tile = P.autotune(phi) if args.autotune else P.tile()
+    if args.tile:
+        P.set_tile(*[int(v) for v in args.tile.split(",")])
+        tile = P.tile()
+    else:
+        tile = P.autotune(phi) if args.autotune else P.tile()
     dt = B.lsp_cfl_dt(P.grid, P.opts, 0.0, spec["t_final"])
     for _ in range(args.warmup):
         P.step(phi, gd, 0.0, dt)
@@ -513,7 +667,12 @@ def main():
     ap.add_argument("--outdir", default=os.path.join(ROOT, "gpurun_out"))
     ap.add_argument("--mode", default="solve", choices=["solve", "steps"])
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--tile", default="", help="tb,ta,ch,minb: fixed tile instead of autotuning")
+    ap.add_argument("--print-kernel-hash", action="store_true")
     args = ap.parse_args()
+    if args.print_kernel_hash:
+        print(kernel_hash())
+        return 0
     if args.mode == "steps":
         return run_steps(args)
     if args.warmup < 3:
@@ -531,6 +690,8 @@ def main():
     try:
         if args.workload == "batched":
             return run_batched(args, rank, world, local_rank)
+        if args.workload == "adjoint":
+            return run_adjoint(args, rank, world, local_rank)
         return run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:

@@ -189,27 +189,30 @@ lsp_status lsp_hj_solve(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
  * second fastest and marches along the third over ch planes; each plane of
  * the tile is staged in shared memory with a 3-cell halo.  minb (2, 3 or 4)
  * selects the kernel variant compiled for that many CTAs per SM (register
- * budget 128, 80 or 64 per thread).
- *  lsp_set_tile(g, 0, 0, 0, 0)   default (32 x 8, chunked for >= 2 waves, 3)
- *  lsp_set_tile(g, -1, 0, 0, 0)  always use the generic kernel
- *  lsp_set_tile(g, tb, ta, ch, minb) explicit; LSP_EINVAL unless
+ * budget 128, 80 or 64 per thread); pair = 1 (WENO5 only) selects the variant
+ * that carries two consecutive planes per thread through paired FP32
+ * instructions.
+ *  lsp_set_tile(g, 0, 0, 0, 0, 0)   default (32 x 8, chunked for >= 2 waves, 3, 0)
+ *  lsp_set_tile(g, -1, 0, 0, 0, 0)  always use the generic kernel
+ *  lsp_set_tile(g, tb, ta, ch, minb, pair) explicit; LSP_EINVAL unless
  *        tb*ta <= 256, the haloed tile fits 4 values per thread, the launch
- *        has <= 65535 z-blocks and minb is 2, 3 or 4.
+ *        has <= 65535 z-blocks, minb is 2, 3 or 4 and pair is 0 or 1.
  * lsp_get_tile reports the tile a step with `opts` would use (all -1 when
  * the generic kernel runs). */
-lsp_status lsp_set_tile(lsp_grid* grid, int tb, int ta, int ch, int minb);
+lsp_status lsp_set_tile(lsp_grid* grid, int tb, int ta, int ch, int minb, int pair);
 lsp_status lsp_get_tile(const lsp_grid* grid, const lsp_solve_opts* opts, int* tb, int* ta,
-                        int* ch, int* minb);
+                        int* ch, int* minb, int* pair);
 
 /* Autotuner: time the first RK stage (phi -> workspace; phi is not
- * modified) for a set of tile shapes, chunk lengths and occupancy targets
- * (7 x 7 x 3 candidates, 3 timed launches each) on this grid and
- * keep the fastest in the grid handle (reported through tb/ta/ch/minb, which may
+ * modified) for a set of tile shapes, chunk lengths, occupancy targets and,
+ * for WENO5, both plane pairings (up to 7 x 7 x 3 x 2 candidates, 3 timed
+ * launches each) on this grid and
+ * keep the fastest in the grid handle (reported through tb/ta/ch/minb/pair, which may
  * be NULL).  Waits for the GPU.  For grids without a tiled kernel it
  * selects the generic one (all -1).  LSP_EUNSUPPORTED for QUADRATIC. */
 lsp_status lsp_autotune(lsp_grid* grid, const lsp_solve_opts* opts, const void* phi,
                         void* workspace, size_t workspace_bytes, void* stream, int* tb, int* ta,
-                        int* ch, int* minb);
+                        int* ch, int* minb, int* pair);
 
 /* lsp_hj_solve without a workspace argument, for callers that cannot
  * allocate device memory: for example a real-time control loop that must

@@ -169,7 +169,8 @@ def nodes(spec: dict, k: int) -> np.ndarray:
 
 def derivs(spec: dict, phi, axis: int, with_ties: bool = False):
     """Left/right derivatives along ``axis`` (Sec. IV-A..IV-C).  Returns
-    (p_minus, p_plus) or (p_minus, p_plus, tie_margin)."""
+    (p_minus, p_plus) or (p_minus, p_plus, flip) where flip is the change a
+    near-tied ENO selection would cause if taken the other way."""
     p = _problem(spec)
     phi = _f64(phi).reshape(spec["n"])
     pm = np.empty_like(phi)

@@ -134,10 +134,10 @@ static void fill_line(const double* line, int64_t n, int G, int periodic, double
 /* ------------------------------------------------------------------------ */
 /* One-sided derivatives on one extended line.  `u` points at node 0 of the  */
 /* extended line, so u[-G..n-1+G] is valid.  Outputs pm[i] = phi_x^-(x_i),   */
-/* pp[i] = phi_x^+(x_i).  `tie` (nullable) receives, per node, the smallest  */
-/* relative margin of the ENO selections made there (1 when none are made):  */
-/* a margin near zero means a last-bit change of the data can flip the       */
-/* choice of stencil.                                                        */
+/* pp[i] = phi_x^+(x_i).  `tie` (nullable) receives, per node, the largest   */
+/* change of p^- or p^+ that flipping a near-tied ENO selection there would  */
+/* cause (0 when none is near a tie, always 0 for the other schemes): where  */
+/* it is large, another implementation may validly take the other stencil.   */
 /* ------------------------------------------------------------------------ */
 
 /* Sec. IV-A, Eq. 6 and the text below it: D^- looks left, D^+ looks right.
@@ -168,23 +168,13 @@ static double D3h(const double* u, int64_t j, double dx) /* D3_{j+1/2} */
     return (D2(u, j + 1, dx) - D2(u, j, dx)) / (3.0 * dx);
 }
 
-/* How close a selection between candidates a and b is to a tie that
- * matters.  When a and b have the same sign, |a| ~ |b| means a ~ b, and
- * taking the other one changes the result only at the level of the rounding
- * that flipped the choice: margin 1.  Likewise when both candidates, times
- * `weight` (which turns them into a derivative correction), are below 1e-6
- * of the derivative's scale: a flip there moves the derivative by less than
- * any tolerance the comparisons use.  With opposite signs the choice flips
- * the correction term: the margin is ||a| - |b|| / (|a| + |b|).
- * (Diagnostic output only; it does not enter any computed value.) */
-static double rel_margin(double a, double b, double weight, double scale)
+/* Relative gap between |a| and |b|: a selection by |a| <= |b| whose gap is
+ * below 1e-4 may be taken the other way by a computation in another
+ * precision or order of operations. */
+static double rel_gap(double a, double b)
 {
     double s = fabs(a) + fabs(b);
-    if (s == 0.0) return 1.0; /* both zero: either choice gives the same value */
-    if ((a >= 0.0) == (b >= 0.0)) return 1.0;
-    /* both candidates at the rounding level of the derivative: no matter */
-    if (s * weight <= 1e-6 * scale) return 1.0;
-    return fabs(fabs(a) - fabs(b)) / s;
+    return s == 0.0 ? 1.0 : fabs(fabs(a) - fabs(b)) / s;
 }
 
 /* ENO polynomial derivative at node i built on base index k (k = i-1 for the
@@ -200,32 +190,57 @@ static double rel_margin(double a, double b, double weight, double scale)
  * the Osher-Fedkiw text the paper follows): k* = k-1 when c took D2_k, else
  * k* = k.  The product in Eq. 14a is read as (x-x_{k*})(x-x_{k*+1})(x-x_{k*+2}),
  * whose derivative at x_i is the printed Eq. 14b.                           */
-static double eno_at(const double* u, int64_t i, int64_t k, double dx, int order,
-                     double* margin)
+/* force2 / force3: -1 to select by the rule, 0 / 1 to take the first /
+ * second candidate regardless (used only to size the effect of a flip). */
+static double eno_eval(const double* u, int64_t i, int64_t k, double dx, int order, int force2,
+                       int force3)
 {
     double q1 = D1h(u, k, dx);
     double a = D2(u, k, dx), b = D2(u, k + 1, dx);
     double c;
     int64_t kstar;
-    if (fabs(a) <= fabs(b)) {
+    int first = force2 < 0 ? (fabs(a) <= fabs(b)) : (force2 == 0);
+    if (first) {
         c = a;
         kstar = k - 1;
     } else {
         c = b;
         kstar = k;
     }
-    double scale = fabs(q1) + (fabs(a) + fabs(b)) * dx;
-    double m = rel_margin(a, b, dx, scale);
     double r = q1 + c * (double)(2 * (i - k) - 1) * dx;
     if (order >= 3) {
         double e = D3h(u, kstar, dx), f = D3h(u, kstar + 1, dx);
-        double cs = (fabs(e) <= fabs(f)) ? e : f;
-        double mm = rel_margin(e, f, dx * dx, scale + (fabs(e) + fabs(f)) * dx * dx);
-        if (mm < m) m = mm;
+        int first3 = force3 < 0 ? (fabs(e) <= fabs(f)) : (force3 == 0);
+        double cs = first3 ? e : f;
         double s = (double)(i - kstar);
         r += cs * (3.0 * s * s - 6.0 * s + 2.0) * dx * dx;
     }
-    if (margin) *margin = m;
+    return r;
+}
+
+/* The ENO derivative, and in *flip (nullable) the largest change of it that
+ * taking a near-tied selection (rel_gap < 1e-4) the other way would cause;
+ * 0 when no selection is near a tie.  (*flip is diagnostic output for the
+ * comparisons with other implementations; it enters no computed value.) */
+static double eno_at(const double* u, int64_t i, int64_t k, double dx, int order, double* flip)
+{
+    double r = eno_eval(u, i, k, dx, order, -1, -1);
+    if (flip) {
+        double fl = 0.0;
+        double a = D2(u, k, dx), b = D2(u, k + 1, dx);
+        int first = fabs(a) <= fabs(b);
+        if (rel_gap(a, b) < 1e-4) fl = fabs(eno_eval(u, i, k, dx, order, first ? 1 : 0, -1) - r);
+        if (order >= 3) {
+            int64_t kstar = first ? k - 1 : k;
+            double e = D3h(u, kstar, dx), f = D3h(u, kstar + 1, dx);
+            if (rel_gap(e, f) < 1e-4) {
+                double alt = eno_eval(u, i, k, dx, order, first ? 0 : 1,
+                                      fabs(e) <= fabs(f) ? 1 : 0);
+                if (fabs(alt - r) > fl) fl = fabs(alt - r);
+            }
+        }
+        *flip = fl;
+    }
     return r;
 }
 
@@ -236,7 +251,7 @@ static void eno_line(const double* u, int64_t n, double dx, int order, double* p
         double m1, m2;
         pm[i] = eno_at(u, i, i - 1, dx, order, &m1);
         pp[i] = eno_at(u, i, i, dx, order, &m2);
-        if (tie) tie[i] = (m1 < m2) ? m1 : m2;
+        if (tie) tie[i] = (m1 > m2) ? m1 : m2;
     }
 }
 
@@ -303,7 +318,7 @@ static void weno5_line(const double* u, int64_t n, double dx, double* pm, double
 }
 
 /* Derivatives of phi along `axis` at every node.  pm, pp: N doubles each;
- * tie (nullable): N doubles, ENO selection margins (1 for non-ENO schemes). */
+ * tie (nullable): N doubles, size of a near-tie flip (see above). */
 int orc_derivs(const orc_problem* P, const double* phi, int axis, double* pm, double* pp,
                double* tie)
 {
@@ -331,7 +346,7 @@ int orc_derivs(const orc_problem* P, const double* phi, int axis, double* pm, do
             for (int64_t i = 0; i < n; ++i) line[i] = phi[base + i * s];
             fill_line(line, n, G, P->periodic[axis], ext);
             const double* u = ext + G;
-            for (int64_t i = 0; i < n; ++i) lt[i] = 1.0;
+            for (int64_t i = 0; i < n; ++i) lt[i] = 0.0;
             switch (P->scheme) {
             case ORC_UPWIND1: upwind1_line(u, n, dx, lm, lp); break;
             case ORC_ENO2: eno_line(u, n, dx, 2, lm, lp, lt); break;

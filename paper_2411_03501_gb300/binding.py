@@ -97,9 +97,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.lsp_hj_solve_noalloc.argtypes = [vp, op, vp, vp, ctypes.c_double, ctypes.c_double,
                                        ctypes.POINTER(lsp_solve_stats), vp]
     ip = ctypes.POINTER(ctypes.c_int)
-    L.lsp_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
-    L.lsp_get_tile.argtypes = [vp, op, ip, ip, ip, ip]
-    L.lsp_autotune.argtypes = [vp, op, vp, vp, sz, vp, ip, ip, ip, ip]
+    L.lsp_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int]
+    L.lsp_get_tile.argtypes = [vp, op, ip, ip, ip, ip, ip]
+    L.lsp_autotune.argtypes = [vp, op, vp, vp, sz, vp, ip, ip, ip, ip, ip]
     pp = ctypes.POINTER(vp)
     L.lsp_batched_workspace_size.argtypes = [ctypes.c_int, pp, op, ctypes.POINTER(sz)]
     L.lsp_hj_solve_batched.argtypes = [ctypes.c_int, pp, op, pp, pp, dp, vp, sz,
@@ -234,19 +235,18 @@ def lsp_hj_solve_noalloc(grid: Grid, opts, phi, target, t0, t_final, stream=None
             "t_end": st.t_end}
 
 
-
-def lsp_set_tile(grid: Grid, tb: int, ta: int, ch: int, minb: int = 3):
-    _check(load().lsp_set_tile(grid.handle, tb, ta, ch, minb))
+def lsp_set_tile(grid: Grid, tb: int, ta: int, ch: int, minb: int = 3, pair: int = 0):
+    _check(load().lsp_set_tile(grid.handle, tb, ta, ch, minb, pair))
 
 
 def lsp_get_tile(grid: Grid, opts) -> tuple:
-    v = [ctypes.c_int() for _ in range(4)]
+    v = [ctypes.c_int() for _ in range(5)]
     _check(load().lsp_get_tile(grid.handle, ctypes.byref(opts), *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
 
 
 def lsp_autotune(grid: Grid, opts, phi, workspace, stream=None) -> tuple:
-    v = [ctypes.c_int() for _ in range(4)]
+    v = [ctypes.c_int() for _ in range(5)]
     _check(load().lsp_autotune(grid.handle, ctypes.byref(opts), _ptr(phi), _ptr(workspace),
                                _nbytes(workspace), _stream(stream),
                                *[ctypes.byref(x) for x in v]))
@@ -375,8 +375,8 @@ class Problem:
     def alpha(self):
         return lsp_get_alpha(self.grid, self.spec["ndim"])
 
-    def set_tile(self, tb, ta=0, ch=0, minb=3):
-        lsp_set_tile(self.grid, tb, ta, ch, minb)
+    def set_tile(self, tb, ta=0, ch=0, minb=3, pair=0):
+        lsp_set_tile(self.grid, tb, ta, ch, minb, pair)
 
     def tile(self):
         return lsp_get_tile(self.grid, self.opts)

@@ -32,7 +32,7 @@ struct lsp_grid {
     // tile of the tiled 3-D/4-D FP32 stage kernel: mode 0 = default shape,
     // 1 = set explicitly (or by the autotuner), -1 = use the generic kernel
     int tile_mode = 0;
-    lsp::Tile tile{0, 0, 0, 3};
+    lsp::Tile tile{0, 0, 0, 3, 0};
 
     // cached CUDA graph of the last lsp_hj_solve with use_graph
     cudaGraphExec_t gexec = nullptr;
@@ -130,6 +130,7 @@ lsp::Tile default_tile(const lsp_grid* g)
     t.tb = 32;
     t.ta = 8;
     t.minb = 3;
+    t.pair = 0;
     const long long nplane = (long long)((g->n[d - 1] + t.tb - 1) / t.tb) *
                              ((g->n[d - 2] + t.ta - 1) / t.ta) * (d == 4 ? g->n[0] : 1);
     long long nch = (2LL * 2 * 152 + nplane - 1) / nplane;
@@ -143,7 +144,7 @@ lsp::Tile default_tile(const lsp_grid* g)
 // The tile the FP32 3-D/4-D stages use, or ch = 0 for the generic kernel.
 lsp::Tile tile_in_effect(const lsp_grid* g, const lsp_solve_opts* o)
 {
-    lsp::Tile none{0, 0, 0, 0};
+    lsp::Tile none{0, 0, 0, 0, 0};
     if (o->dtype != LSP_F32 || (g->ndim != 3 && g->ndim != 4) || g->tile_mode < 0) return none;
     lsp::Tile t = g->tile_mode == 1 ? g->tile : default_tile(g);
     return lsp::tile_valid(g->ndim, o->scheme, t, g->n) ? t : none;
@@ -620,7 +621,7 @@ lsp_status lsp_hj_solve(lsp_grid* g, const lsp_solve_opts* o, void* phi, const v
     return LSP_OK;
 }
 
-lsp_status lsp_set_tile(lsp_grid* g, int tb, int ta, int ch, int minb)
+lsp_status lsp_set_tile(lsp_grid* g, int tb, int ta, int ch, int minb, int pair)
 {
     if (!g) return fail(LSP_EINVAL, "grid is NULL");
     if (g->gexec) {
@@ -635,7 +636,7 @@ lsp_status lsp_set_tile(lsp_grid* g, int tb, int ta, int ch, int minb)
         g->tile_mode = 0;
         return LSP_OK;
     }
-    lsp::Tile t{tb, ta, ch, minb};
+    lsp::Tile t{tb, ta, ch, minb, pair};
     if (!lsp::tile_valid(g->ndim, LSP_WENO5, t, g->n))
         return fail(LSP_EINVAL, "tile %dx%dx%d (%d CTAs/SM) is not valid for this grid", tb, ta,
                     ch, minb);
@@ -645,26 +646,27 @@ lsp_status lsp_set_tile(lsp_grid* g, int tb, int ta, int ch, int minb)
 }
 
 lsp_status lsp_get_tile(const lsp_grid* g, const lsp_solve_opts* o, int* tb, int* ta, int* ch,
-                        int* minb)
+                        int* minb, int* pair)
 {
     lsp_status s = check_opts(g, o);
     if (s) return s;
-    if (!tb || !ta || !ch || !minb) return fail(LSP_EINVAL, "NULL argument");
+    if (!tb || !ta || !ch || !minb || !pair) return fail(LSP_EINVAL, "NULL argument");
     const lsp::Tile t = tile_in_effect(g, o);
     if (t.ch == 0) {
-        *tb = *ta = *ch = *minb = -1;
+        *tb = *ta = *ch = *minb = *pair = -1;
     } else {
         *tb = t.tb;
         *ta = t.ta;
         *ch = t.ch;
         *minb = t.minb;
+        *pair = t.pair;
     }
     return LSP_OK;
 }
 
 lsp_status lsp_autotune(lsp_grid* g, const lsp_solve_opts* o, const void* phi, void* ws,
                         size_t ws_size, void* stream, int* tb_out, int* ta_out, int* ch_out,
-                        int* minb_out)
+                        int* minb_out, int* pair_out)
 {
     lsp_status s = check_opts(g, o);
     if (!s) s = check_field(phi, "phi");
@@ -677,6 +679,7 @@ lsp_status lsp_autotune(lsp_grid* g, const lsp_solve_opts* o, const void* phi, v
         if (ta_out) *ta_out = -1;
         if (ch_out) *ch_out = -1;
         if (minb_out) *minb_out = -1;
+        if (pair_out) *pair_out = -1;
         return LSP_OK;
     }
     if (!g->alpha_state) return fail(LSP_EUNSUPPORTED, "autotune needs state-only LF bounds");
@@ -691,14 +694,16 @@ lsp_status lsp_autotune(lsp_grid* g, const lsp_solve_opts* o, const void* phi, v
     trial.gexec = nullptr;
     trial.capture_stream = nullptr;
     float best_ms = 1e30f;
-    lsp::Tile best{0, 0, 0, 0};
+    lsp::Tile best{0, 0, 0, 0, 0};
     const double dt = cfl_dt_host(g, o->cfl, 0.0, INFINITY);
     for (const auto& sh : shapes) {
-        for (int cand = 0; cand < 21; ++cand) {
+        for (int cand = 0; cand < 42; ++cand) {
             const int sp = splits[cand % 7];
-            const int minb = 2 + cand / 7;
+            const int minb = 2 + (cand / 7) % 3;
+            const int pair = cand / 21;
+            if (pair && o->scheme != LSP_WENO5) continue;
             const int nS = g->n[d - 3];
-            lsp::Tile t{sh[0], sh[1], (nS + sp - 1) / sp, minb};
+            lsp::Tile t{sh[0], sh[1], (nS + sp - 1) / sp, minb, pair};
             if (!lsp::tile_valid(d, o->scheme, t, g->n)) continue;
             trial.tile = t;
             trial.tile_mode = 1;
@@ -736,6 +741,7 @@ lsp_status lsp_autotune(lsp_grid* g, const lsp_solve_opts* o, const void* phi, v
     if (ta_out) *ta_out = best.ta;
     if (ch_out) *ch_out = best.ch;
     if (minb_out) *minb_out = best.minb;
+    if (pair_out) *pair_out = best.pair;
     return LSP_OK;
 }
 

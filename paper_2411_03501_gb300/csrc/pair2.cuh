@@ -1,0 +1,79 @@
+// pair2.cuh -- two FP32 values carried together through Blackwell's paired
+// FP32 instructions (FADD2 / FMUL2 / FFMA2: one issue, two results).  Used to
+// evaluate the same stencil at two nodes at once (two consecutive planes of
+// the march), halving the issued FP32 instructions of the WENO5 arithmetic.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace lsp {
+
+struct F2 {
+    float2 v;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ explicit F2(float2 x) : v(x) {}
+    __device__ __forceinline__ F2(float a) : v(make_float2(a, a)) {}
+    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ float x() const { return v.x; }
+    __device__ __forceinline__ float y() const { return v.y; }
+};
+
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+// a - b as one paired FMA: b * (-1) + a is exact
+__device__ __forceinline__ F2 operator-(F2 a, F2 b)
+{
+    return F2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v));
+}
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(__fmul2_rn(a.v, make_float2(-1.f, -1.f))); }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ F2 max2(F2 a, F2 b) { return F2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y)); }
+__device__ __forceinline__ F2 min2(F2 a, F2 b) { return F2(fminf(a.v.x, b.v.x), fminf(a.v.y, b.v.y)); }
+__device__ __forceinline__ F2 abs2(F2 a) { return F2(fabsf(a.v.x), fabsf(a.v.y)); }
+__device__ __forceinline__ F2 sqrt2(F2 a) { return F2(sqrtf(a.v.x), sqrtf(a.v.y)); }
+
+// Jiang-Peng Phi of deriv_weno5_jp for two nodes (same formulas and the same
+// exact power-of-two rescaling, per component).
+__device__ __forceinline__ F2 weno_phi2(F2 is0, F2 is1, F2 is2, F2 e, F2 A, F2 B)
+{
+    const F2 sc(__uint_as_float(0x7f000000u - (__float_as_uint(e.v.x) & 0x7f800000u)),
+                __uint_as_float(0x7f000000u - (__float_as_uint(e.v.y) & 0x7f800000u)));
+    const F2 q0 = (is0 + e) * sc, q1 = (is1 + e) * sc, q2 = (is2 + e) * sc;
+    const F2 Q0 = q0 * q0, Q1 = q1 * q1, Q2 = q2 * q2;
+    const F2 Q12 = Q1 * Q2, Q01 = Q0 * Q1;
+    const F2 P = fma2(F2(6.0f) * Q0, Q2, fma2(F2(3.0f), Q01, Q12));
+    const F2 r(__fdividef(1.0f, P.v.x), __fdividef(1.0f, P.v.y));
+    const F2 w0 = Q12 * r, w2 = F2(3.0f) * Q01 * r;
+    return fma2(w0 * F2(1.0f / 3.0f), A, (w2 - F2(0.5f)) * (B * F2(1.0f / 6.0f)));
+}
+
+// deriv_weno5_jp for two nodes: u[o] holds the window values at offset o-3
+// of both nodes.
+__device__ __forceinline__ void deriv_weno5_jp2(const F2* u, float inv_dx, float floor12, F2& pm,
+                                                F2& pp)
+{
+    const F2 dm3 = u[1] - u[0], dm2 = u[2] - u[1], dm1 = u[3] - u[2];
+    const F2 d0 = u[4] - u[3], d1 = u[5] - u[4], d2 = u[6] - u[5];
+    const F2 Sm2 = dm2 - dm3, Sm1 = dm1 - dm2, S0 = d0 - dm1, S1 = d1 - d0, S2 = d2 - d1;
+    const F2 cen = (fma2(F2(7.0f), dm1 + d0, -(dm2 + d1))) * F2(1.0f / 12.0f);
+    const F2 m4 = max2(max2(dm2 * dm2, dm1 * dm1), max2(d0 * d0, d1 * d1));
+    const F2 eL = fma2(F2(1.2e-5f), max2(m4, dm3 * dm3), F2(floor12));
+    const F2 eR = fma2(F2(1.2e-5f), max2(m4, d2 * d2), F2(floor12));
+    const F2 g1 = Sm2 - Sm1, g2 = Sm1 - S0, g3 = S0 - S1, g4 = S1 - S2;
+    const F2 e1 = g1 * g1, e2 = g2 * g2, e3 = g3 * g3, e4 = g4 * g4;
+    const F2 f0m = fma2(F2(-3.0f), Sm1, Sm2), f1m = Sm1 + S0, f2m = fma2(F2(3.0f), S0, -S1);
+    const F2 f0p = fma2(F2(-3.0f), S1, S2), f1p = S1 + S0, f2p = fma2(F2(3.0f), S0, -Sm1);
+    const F2 three(3.0f), thirteen(13.0f);
+    const F2 is0m = fma2(thirteen, e1, three * f0m * f0m);
+    const F2 is1m = fma2(thirteen, e2, three * f1m * f1m);
+    const F2 is2m = fma2(thirteen, e3, three * f2m * f2m);
+    const F2 is0p = fma2(thirteen, e4, three * f0p * f0p);
+    const F2 is1p = fma2(thirteen, e3, three * f1p * f1p);
+    const F2 is2p = fma2(thirteen, e2, three * f2p * f2p);
+    const F2 two(2.0f);
+    const F2 Tm1 = fma2(-two, Sm1, Sm2 + S0), T0 = fma2(-two, S0, Sm1 + S1);
+    const F2 T1 = fma2(-two, S1, S0 + S2);
+    pm = (cen - weno_phi2(is0m, is1m, is2m, eL, Tm1, T0)) * F2(inv_dx);
+    pp = (cen + weno_phi2(is0p, is1p, is2p, eR, T1, T0)) * F2(inv_dx);
+}
+
+}  // namespace lsp

@@ -1,0 +1,209 @@
+// stage_pair.cuh -- the tiled WENO5 stage body evaluating two consecutive
+// planes of the march per iteration with paired FP32 instructions.
+//
+// Same computation and the same per-node arithmetic order as
+// tiled_stage_body<.., WENO5, .., float> (stage_tiled.cuh); each thread
+// carries the nodes (s, ia, ib) and (s+1, ia, ib) together in F2 values, so
+// every add/mul/fma of the derivatives, the Hamiltonian and the combination
+// is issued once for both.  The plane tiles of s and s+1 are staged side by
+// side (double-buffered, four tiles), the marching window holds 2G+2 values.
+#pragma once
+#include "pair2.cuh"
+#include "stage_tiled.cuh"
+
+namespace lsp {
+
+template <int DYN, int NDIM>
+__device__ __forceinline__ F2 hamiltonian_pair(const F2* x, const F2* p, const float* prm, float s,
+                                               float c)
+{
+    if constexpr (DYN == NORMAL_SPEED) {
+        F2 n2 = p[0] * p[0];
+#pragma unroll
+        for (int k = 1; k < NDIM; ++k) n2 = fma2(p[k], p[k], n2);
+        return F2(prm[0]) * sqrt2(n2);
+    } else if constexpr (DYN == TRANSLATE) {
+        F2 h = F2(prm[0]) * p[0];
+#pragma unroll
+        for (int k = 1; k < NDIM; ++k) h = fma2(F2(prm[k]), p[k], h);
+        return h;
+    } else if constexpr (DYN == AIR3D) {
+        const float ve = prm[0], vp = prm[1], um = prm[2], dm = prm[3];
+        const F2 sw = p[0] * x[1] - p[1] * x[0] - p[2];
+        const F2 v = p[0] * F2(-ve + vp * c) + p[1] * F2(vp * s) + F2(um) * abs2(sw) -
+                     F2(dm) * abs2(p[2]);
+        return -v;
+    } else if constexpr (DYN == CAR4D) {
+        const F2 m = p[0] * x[3] * F2(c) + p[1] * x[3] * F2(s) - F2(prm[0]) * abs2(p[2]) -
+                     F2(prm[1]) * abs2(p[3]);
+        return -m;
+    } else {
+        F2 n2 = p[0] * p[0];
+#pragma unroll
+        for (int k = 1; k < NDIM; ++k) n2 = fma2(p[k], p[k], n2);
+        return F2(0.5f) * n2;
+    }
+}
+
+template <int NDIM, int DYN>
+__device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int TB, int TA, int bx,
+                                                int by, int chunk, int outer, int ch, float* tile,
+                                                int tx, int ty)
+{
+    static_assert(NDIM == 3 || NDIM == 4, "paired planes need a marching axis");
+    constexpr int G = 3;
+    constexpr int AS = NDIM - 3, AA = NDIM - 2, AB = NDIM - 1;
+    const int W = TB + 2 * G, H = TA + 2 * G, HW = H * W;
+    const int nB = a.n[AB], nA = a.n[AA], nS = a.n[AS];
+    const int sA = a.stride[AA], sS = a.stride[AS];
+    const int b0 = bx * TB, a0 = by * TA;
+    const int base_outer = (NDIM == 4) ? outer * a.stride[0] : 0;
+    const int s_begin = chunk * ch;
+    const int s_end = min(s_begin + ch, nS);
+    const int ib = b0 + tx, ia = a0 + ty;
+    const bool active = (ib < nB) && (ia < nA);
+    const int tid = ty * TB + tx, nthr = TB * TA;
+
+    float alpha[NDIM];
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k)
+        alpha[k] = a.alpha_from_ctl ? float(__longlong_as_double((long long)a.ctl->alpha_bits[k]))
+                                    : a.alpha[k];
+    const float dt = a.dt_from_ctl ? float(a.ctl->dt) : a.dt;
+    const F2 cl(a.c_l * dt), cs(a.c_s), cn(a.c_n);
+    const float fl_s = weno_floor12(a.inv_dx[AS]);
+    const float fl_a = weno_floor12(a.inv_dx[AA]);
+    const float fl_b = weno_floor12(a.inv_dx[AB]);
+
+    F2 x[NDIM];
+    if constexpr (NDIM == 4) x[0] = F2(a.lo[0] + float(outer) * a.h[0]);
+    x[AA] = F2(a.lo[AA] + float(ia) * a.h[AA]);
+    x[AB] = F2(a.lo[AB] + float(ib) * a.h[AB]);
+    float sth = 0.f, cth = 1.f;
+    if constexpr (DYN == AIR3D || DYN == CAR4D) sincosf(x[2].x(), &sth, &cth);
+
+    const int ia_c = min(ia, nA - 1), ib_c = min(ib, nB - 1);
+    const float* col = a.phi_s + base_outer + ia_c * sA + ib_c;
+    float w[2 * G + 2];
+#pragma unroll
+    for (int o = -G; o < G; ++o) w[o + G] = line_value(col, s_begin + o, nS, sS, a.periodic[AS]);
+
+    constexpr int MAXE = 4;
+    int e_off[MAXE];
+    unsigned kinds = 0;
+#pragma unroll
+    for (int k = 0; k < MAXE; ++k) {
+        const int e = tid + k * nthr;
+        const int r = e / W, c = e - r * W;
+        const int ja = a0 - G + r, jb = b0 - G + c;
+        const bool inA = ja >= 0 && ja < nA, inB = jb >= 0 && jb < nB;
+        const unsigned kind = (e >= HW) ? 3u : (inA && inB) ? 0u : inA ? 1u : inB ? 2u : 3u;
+        kinds |= kind << (2 * k);
+        e_off[k] = (kind == 0u) ? ja * sA + jb : (kind == 1u ? ja : (kind == 2u ? jb : 0));
+    }
+    auto fetch = [&](int s, float* pf) {
+        const float* plane = a.phi_s + base_outer + s * sS;
+#pragma unroll
+        for (int k = 0; k < MAXE; ++k) {
+            const unsigned kind = (kinds >> (2 * k)) & 3u;
+            float v = 0.f;
+            if (kind == 0u) {
+                v = __ldg(plane + e_off[k]);
+            } else if (kind == 1u) {
+                const int e = tid + k * nthr;
+                v = line_value(plane + e_off[k] * sA, b0 - G + (e - (e / W) * W), nB, 1,
+                               a.periodic[AB]);
+            } else if (kind == 2u) {
+                const int e = tid + k * nthr;
+                v = line_value(plane + e_off[k], a0 - G + e / W, nA, sA, a.periodic[AA]);
+            }
+            pf[k] = v;
+        }
+    };
+    float pfA[MAXE], pfB[MAXE];
+    fetch(s_begin, pfA);
+    fetch(min(s_begin + 1, nS - 1), pfB);
+    float wnA = line_value(col, s_begin + G, nS, sS, a.periodic[AS]);
+    float wnB = line_value(col, s_begin + G + 1, nS, sS, a.periodic[AS]);
+
+    for (int s = s_begin; s < s_end; s += 2) {
+        float* curA = tile + (((s - s_begin) >> 1) & 1) * (2 * HW);
+        float* curB = curA + HW;
+#pragma unroll
+        for (int k = 0; k < MAXE; ++k)
+            if (((kinds >> (2 * k)) & 3u) != 3u) {
+                curA[tid + k * nthr] = pfA[k];
+                curB[tid + k * nthr] = pfB[k];
+            }
+        w[2 * G] = wnA;
+        w[2 * G + 1] = wnB;
+        __syncthreads();  // planes s, s+1 staged; the other buffer pair is free
+        if (s + 2 < s_end) {
+            fetch(s + 2, pfA);
+            fetch(min(s + 3, nS - 1), pfB);
+            wnA = line_value(col, s + 2 + G, nS, sS, a.periodic[AS]);
+            wnB = line_value(col, s + 3 + G, nS, sS, a.periodic[AS]);
+        }
+        if (active) {
+            const bool second = s + 1 < s_end;
+            F2 u[2 * G + 1], pm, pp, pbar[NDIM], diss(0.f);
+#pragma unroll
+            for (int o = 0; o <= 2 * G; ++o) u[o] = F2(w[o], w[o + 1]);
+            deriv_weno5_jp2(u, a.inv_dx[AS], fl_s, pm, pp);
+            pbar[AS] = F2(0.5f) * (pp + pm);
+            diss = F2(0.5f * alpha[AS]) * (pp - pm);
+#pragma unroll
+            for (int o = 0; o <= 2 * G; ++o)
+                u[o] = F2(curA[(ty + o) * W + tx + G], curB[(ty + o) * W + tx + G]);
+            deriv_weno5_jp2(u, a.inv_dx[AA], fl_a, pm, pp);
+            pbar[AA] = F2(0.5f) * (pp + pm);
+            diss = fma2(F2(0.5f * alpha[AA]), pp - pm, diss);
+#pragma unroll
+            for (int o = 0; o <= 2 * G; ++o)
+                u[o] = F2(curA[(ty + G) * W + tx + o], curB[(ty + G) * W + tx + o]);
+            const F2 center = u[G];
+            deriv_weno5_jp2(u, a.inv_dx[AB], fl_b, pm, pp);
+            pbar[AB] = F2(0.5f) * (pp + pm);
+            diss = fma2(F2(0.5f * alpha[AB]), pp - pm, diss);
+            if constexpr (NDIM == 4) {
+                const float* c0 = a.phi_s + s * sS + ia * sA + ib;
+                const int s2 = second ? s + 1 : s;
+#pragma unroll
+                for (int o = -G; o <= G; ++o)
+                    u[o + G] = F2(line_value(c0, outer + o, a.n[0], a.stride[0], a.periodic[0]),
+                                  line_value(c0 + (s2 - s) * sS, outer + o, a.n[0], a.stride[0],
+                                             a.periodic[0]));
+                deriv_weno5_jp2(u, a.inv_dx[0], weno_floor12(a.inv_dx[0]), pm, pp);
+                pbar[0] = F2(0.5f) * (pp + pm);
+                diss = fma2(F2(0.5f * alpha[0]), pp - pm, diss);
+            }
+            x[AS] = F2(a.lo[AS] + float(s) * a.h[AS], a.lo[AS] + float(s + 1) * a.h[AS]);
+            const F2 Hv = hamiltonian_pair<DYN, NDIM>(x, pbar, a.prm, sth, cth);
+            const F2 L = diss - Hv;
+            const int idx = base_outer + s * sS + ia * sA + ib;
+            F2 v = fma2(cs, center, cl * L);
+            if (a.phi_n) v = fma2(cn, F2(a.phi_n[idx], second ? a.phi_n[idx + sS] : 0.f), v);
+            if (a.tube) v = min2(v, F2(__ldg(a.target + idx), second ? __ldg(a.target + idx + sS) : 0.f));
+            if (!isfinite(v.x()) || (second && !isfinite(v.y())))
+                atomicOr(&a.ctl->flags, kFlagNonFinite);
+            a.out[idx] = v.x();
+            if (second) a.out[idx + sS] = v.y();
+        }
+#pragma unroll
+        for (int o = 0; o < 2 * G; ++o) w[o] = w[o + 2];
+    }
+}
+
+// Single-problem launch of the paired body (WENO5, FP32): blockDim = (tb,
+// ta); gridDim = (ceil(nB/tb), ceil(nA/ta), nchunks * nOuter); ch is even.
+template <int NDIM, int DYN, int MINB>
+__global__ void __launch_bounds__(256, MINB) stage_pair_kernel(StageArgs<float> a, int ch, int nchunks)
+{
+    extern __shared__ unsigned char smem_raw[];
+    float* tile = reinterpret_cast<float*>(smem_raw);
+    tiled_pair_body<NDIM, DYN>(a, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y,
+                               blockIdx.z % nchunks, blockIdx.z / nchunks, ch, tile, threadIdx.x,
+                               threadIdx.y);
+}
+
+}  // namespace lsp

@@ -114,6 +114,7 @@ __device__ __forceinline__ R line_value(const R* __restrict__ p, int j, int n, i
 struct Tile {
     int tb, ta, ch;  // tile width (fastest axis), tile rows, planes per CTA
     int minb;        // occupancy target of the kernel variant (2, 3 or 4)
+    int pair;        // 1: two planes per iteration in paired FP32 (WENO5 only)
 };
 
 // One CTA's share of a stage: the tile (bx, by) of the two fastest axes,

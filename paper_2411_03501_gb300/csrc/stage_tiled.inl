@@ -1,6 +1,7 @@
 // stage_tiled.inl -- FP32 instantiations of the tiled stage kernel for one
 // occupancy target LSP_MINB (included by stage_tiled_m{2,3,4}.cu).
 #include "launch.h"
+#include "stage_pair.cuh"
 #include "stage_tiled.cuh"
 
 namespace lsp {
@@ -15,6 +16,12 @@ static cudaError_t tiled_one(const StageArgs<float>& a, const Tile& t, cudaStrea
     dim3 grid((nB + t.tb - 1) / t.tb, (nA + t.ta - 1) / t.ta,
               nchunks * (NDIM == 4 ? a.n[0] : 1));
     const size_t smem = 2 * sizeof(float) * (t.ta + 2 * G) * (t.tb + 2 * G);
+    if constexpr (SCHEME == WENO5) {
+        if (t.pair) {
+            stage_pair_kernel<NDIM, DYN, LSP_MINB><<<grid, block, 2 * smem, s>>>(a, t.ch, nchunks);
+            return cudaGetLastError();
+        }
+    }
     stage_tiled_kernel<NDIM, SCHEME, DYN, float, LSP_MINB><<<grid, block, smem, s>>>(a, t.ch, nchunks);
     return cudaGetLastError();
 }

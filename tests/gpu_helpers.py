@@ -11,7 +11,8 @@ The tests allow 8 times that:
     tol_rate = 8 * (16 u max|phi| sum_k alpha_k / dx_k + u max|L|).
 A stage adds dt times that plus the rounding of the combination.  Where an
 ENO stencil choice is within 1e-4 (relative) of a tie, the FP32 and FP64
-choices may differ; those nodes are compared separately (they must be few).
+choices may differ; there the bar grows by what the other stencil changes
+(flip_allowance), and such nodes must be few.
 """
 import numpy as np
 import torch
@@ -42,13 +43,58 @@ def gpu_rate(spec, phi):
     return out.double().cpu().numpy(), P
 
 
-def tie_margin(spec, phi):
-    m = np.ones(spec["n"])
+def flip_allowance(spec, phi, alpha):
+    """Per node, how much the rate L may validly differ because a near-tied
+    ENO selection can go either way in another precision: the oracle reports
+    the change of p-/p+ a flip would cause (flip_k); the rate moves by at most
+    sum_k alpha_k (|dp+_k| + |dp-_k|) <= 2 sum_k alpha_k flip_k.  Zero for the
+    schemes without selections."""
+    out = np.zeros(spec["n"])
     if spec["scheme"] in ("eno2", "eno3"):
         for k in range(spec["ndim"]):
-            _, _, t = oracle.derivs(spec, phi, k, with_ties=True)
-            m = np.minimum(m, t)
-    return m
+            _, _, f = oracle.derivs(spec, phi, k, with_ties=True)
+            out += 2.0 * float(alpha[k]) * f
+    return out
+
+
+def dilate(a, spec, width=3):
+    """Running max over +-width nodes along every axis (periodic axes wrap,
+    others clamp): an error in a stage field reaches the stencils of the
+    neighbours within that width in the next stage."""
+    out = a.copy()
+    for k in range(spec["ndim"]):
+        cur = out.copy()
+        for sh in range(1, width + 1):
+            for sgn in (1, -1):
+                r = np.roll(out, sgn * sh, axis=k)
+                if not spec["periodic"][k]:
+                    idx = [slice(None)] * spec["ndim"]
+                    idx[k] = slice(0, sh) if sgn > 0 else slice(-sh, None)
+                    r[tuple(idx)] = 0.0
+                cur = np.maximum(cur, r)
+        out = cur
+    return out
+
+
+def step_flip_allowance(spec, phi, dt, rk, alpha, tol, max_frac=0.05):
+    """The same for one RK step: the flip allowances of the stage inputs
+    (phi, W1, W2 as the oracle computes them), weighted by dt, spread over the
+    stencil width and doubled for what the next stages make of them.  Checks
+    that at most max_frac of the nodes carry a flip larger than tol before
+    the spreading."""
+    if spec["scheme"] not in ("eno2", "eno3"):
+        return np.zeros(spec["n"])
+    u = [np.asarray(phi, dtype=np.float64)]
+    L0, _ = oracle.rate(spec, u[0])
+    if rk >= 2:
+        u.append(u[0] + dt * L0)
+    if rk >= 3:
+        L1, _ = oracle.rate(spec, u[1])
+        u.append(0.75 * u[0] + 0.25 * (u[1] + dt * L1))
+    tot = sum(flip_allowance(spec, ui, alpha) for ui in u)
+    frac = float((2.0 * dt * tot > tol).mean())
+    assert frac <= max_frac, f"{frac:.3%} of nodes near an ENO tie"
+    return 2.0 * dt * dilate(tot, spec)
 
 
 def rate_tol(spec, phi, L, alpha):
@@ -104,23 +150,19 @@ def sign_ok(got, want, spec):
     return not (((got > 0) != s) & ~near).any()
 
 
-def compare(got, want, tol, ties=None, max_tie_frac=0.02, tie_bound=None):
-    """Element-wise |got - want| <= tol, except nodes near an ENO tie, which
-    must be rare (at most max_tie_frac) and within tie_bound (default: half
-    the largest |want| plus tol -- a flipped choice between candidates of
-    opposite sign moves the derivative by up to twice their magnitude)."""
+def compare(got, want, tol, allowance=None, max_frac=1.0):
+    """Element-wise |got - want| <= tol + allowance.  `allowance` (per node,
+    from flip_allowance / step_flip_allowance) admits the other valid ENO
+    stencil where a selection is near a tie; the nodes where it exceeds tol
+    must be at most max_frac (flip_allowance callers pass 0.05; the spread
+    step allowance checks its own count before spreading)."""
     err = np.abs(got - want)
-    if ties is None:
-        assert np.isfinite(got).all()
-        assert err.max() <= tol, f"max err {err.max():.3e} > tol {tol:.3e} at {np.unravel_index(err.argmax(), err.shape)}"
-        return err.max()
-    near = ties < 1e-4
-    assert near.mean() <= max_tie_frac, f"{near.mean():.3%} of nodes near an ENO tie"
-    far = ~near
-    if far.any():
-        e = err[far].max()
-        assert e <= tol, f"max err {e:.3e} > tol {tol:.3e} away from ties"
-    if near.any():
-        bound = tie_bound if tie_bound is not None else 0.5 * np.abs(want).max() + tol
-        assert np.isfinite(got[near]).all() and err[near].max() <= bound
-    return err[far].max() if far.any() else 0.0
+    assert np.isfinite(got).all()
+    bound = tol if allowance is None else tol + allowance
+    bad = err > bound
+    assert not bad.any(), (f"max excess {(err - bound).max():.3e} (tol {tol:.3e}) at "
+                           f"{np.unravel_index((err - bound).argmax(), err.shape)}")
+    if allowance is not None:
+        frac = float((allowance > tol).mean())
+        assert frac <= max_frac, f"{frac:.3%} of nodes near an ENO tie"
+    return float(err.max())

@@ -65,8 +65,11 @@ def test_fp64_adjoint_matches_oracle(kind, scheme, rk):
     assert np.abs(phiT - ophiT).max() <= 1e-11 * np.abs(ophiT).max()
     assert np.abs(lam0 - o0).max() <= 1e-9 * np.abs(o0).max(), np.abs(lam0 - o0).max()
     assert np.abs(lamg - og).max() <= 1e-9 * max(np.abs(og).max(), 1e-300)
+    # parameter gradients may vanish (normal speed: dt L does not depend on
+    # the speed); the absolute floor follows the scale of the field gradient
     npar = len(spec["params"])
-    np.testing.assert_allclose(dprm[:npar], oprm[:npar], rtol=1e-8, atol=1e-9 * np.abs(oprm).max())
+    floor = 1e-9 * max(np.abs(oprm).max(), np.abs(o0).max())
+    np.testing.assert_allclose(dprm[:npar], oprm[:npar], rtol=1e-8, atol=floor)
 
 
 @pytest.mark.parametrize("kind,scheme,rk", CASES[:2] + CASES[4:])
@@ -78,7 +81,8 @@ def test_fp32_adjoint_matches_oracle(kind, scheme, rk):
     assert np.abs(lam0 - o0).max() <= 1e-4 * np.abs(o0).max(), np.abs(lam0 - o0).max()
     assert np.abs(lamg - og).max() <= 1e-4 * max(np.abs(og).max(), 1e-30)
     npar = len(spec["params"])
-    np.testing.assert_allclose(dprm[:npar], oprm[:npar], rtol=1e-3, atol=1e-4 * np.abs(oprm).max())
+    floor = 1e-4 * max(np.abs(oprm).max(), np.abs(o0).max())
+    np.testing.assert_allclose(dprm[:npar], oprm[:npar], rtol=1e-3, atol=floor)
 
 
 def test_checkpoint_counts_agree():
@@ -135,20 +139,29 @@ def test_autograd_matches_central_differences_fp64():
 
 @pytest.mark.slow
 def test_adjoint_workload_fp32_against_fd_and_fp64():
-    """The differentiation workload: air3d tube at 129^3, 200 RK3 steps, FP32,
-    loss = smoothed volume + values at 1024 seeded query states.  Gradients
-    with respect to v_e, v_p, the shared turn-rate bound and the target
-    radius: against central differences (h = 1e-3) of the FP32 forward, and
-    against the FP64 adjoint of the same solve."""
+    """The differentiation workload: air3d tube at 129^3, 200 RK3 steps,
+    loss = smoothed volume + values at 1024 seeded query states; gradients
+    with respect to v_e, v_p, the shared turn-rate bound w and the target
+    radius r.
+
+    * FP64 adjoint against FP64 central differences with h = 1e-6 (1e-5
+      relative): the discrete map is piecewise smooth (input signs, the min
+      with the target, ENO/WENO selections switch), so finite differences
+      converge to the adjoint only once h is below the distance to the
+      nearest switch -- at h = 1e-3 they are off by ~2% on v_p even in FP64.
+    * FP32 adjoint against the FP64 adjoint (2e-2 relative: the v_p
+      gradient is a small difference of large terms) and against FP32
+      central differences with h = 1e-3 (6e-2 relative: the kinks above plus
+      FP32 rounding of the loss)."""
     n, nsteps = 129, 200
     res = {}
-    for dtype in ("f32", "f64"):
+    fd = {}
+    for dtype, h in (("f64", 1e-6), ("f32", 1e-3)):
         spec, sdf, q = _air3d_adjoint_problem(n, nsteps, dtype)
         tube = HJTube(spec, nsteps=nsteps)
         tdt = torch.float64 if dtype == "f64" else torch.float32
         sdf_t = torch.as_tensor(sdf, device="cuda").to(tdt)
         q_t = torch.as_tensor(q, device="cuda").to(tdt)
-        # the shared turn-rate bound w enters as (v_e, v_p, w, w)
         base = torch.tensor([5.0, 5.0, 1.0], dtype=torch.float64, requires_grad=True)
         r = torch.tensor(5.0, dtype=torch.float64, requires_grad=True)
 
@@ -159,20 +172,17 @@ def test_adjoint_workload_fp32_against_fd_and_fp64():
 
         L = run(base, r)
         L.backward()
-        res[dtype] = (L.item(), base.grad.numpy().copy(), r.grad.item())
-        if dtype == "f32":
-            h = 1e-3
-            with torch.no_grad():
-                for j in range(3):
-                    bp = base.detach().clone()
-                    bm = base.detach().clone()
-                    bp[j] += h
-                    bm[j] -= h
-                    fd = (run(bp, r) - run(bm, r)).item() / (2 * h)
-                    g = res["f32"][1][j]
-                    assert abs(fd - g) <= 2e-2 * abs(fd) + 1e-2, (j, fd, g)
-                fd = (run(base, r + h) - run(base, r - h)).item() / (2 * h)
-                assert abs(fd - res["f32"][2]) <= 2e-2 * abs(fd) + 1e-2, (fd, res["f32"][2])
-    g32, g64 = res["f32"], res["f64"]
-    np.testing.assert_allclose(g32[1], g64[1], rtol=1e-2, atol=1e-3 * np.abs(g64[1]).max())
-    assert abs(g32[2] - g64[2]) <= 1e-2 * abs(g64[2]) + 1e-3
+        res[dtype] = np.concatenate([base.grad.numpy(), [r.grad.item()]])
+        vals = []
+        with torch.no_grad():
+            for j in range(3):
+                bp = base.detach().clone()
+                bm = base.detach().clone()
+                bp[j] += h
+                bm[j] -= h
+                vals.append((run(bp, r) - run(bm, r)).item() / (2 * h))
+            vals.append((run(base, r + h) - run(base, r - h)).item() / (2 * h))
+        fd[dtype] = np.array(vals)
+    np.testing.assert_allclose(res["f64"], fd["f64"], rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(res["f32"], res["f64"], rtol=2e-2, atol=1e-3)
+    np.testing.assert_allclose(res["f32"], fd["f32"], rtol=6e-2, atol=1e-2)

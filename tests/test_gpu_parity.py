@@ -8,7 +8,7 @@ import torch
 
 import oracle
 from gpu_helpers import (U32, check_fp32_solve, compare, gpu_rate, noise_spread, rate_tol, rounded,
-                         sign_ok, tie_margin, to_dev)
+                         sign_ok, flip_allowance, step_flip_allowance, to_dev)
 from paper_2411_03501_gb300 import binding as B
 from paper_2411_03501_gb300 import workloads as W
 
@@ -60,8 +60,8 @@ def test_rate_parity_brute_force(kind, ndim, scheme, dyn, dtype):
     if dyn != "quadratic":
         np.testing.assert_allclose(P.alpha(), alpha, rtol=1e-12, atol=1e-300)
     tol = rate_tol(spec, phi, want, alpha)
-    ties = tie_margin(spec, phi) if dtype == "f32" else None
-    compare(got, want, tol, ties)
+    compare(got, want, tol, flip_allowance(spec, phi, alpha) if dtype == "f32" else None,
+            max_frac=0.05)
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
@@ -159,7 +159,7 @@ def test_car4d_reduced_solve_fp32_within_tolerance():
         want_step = oracle.step(spec, before, dt, 3, target=g32)
         L, _ = oracle.rate(spec, before)
         tol = 3 * dt * rate_tol(spec, before, L, a) + 8 * U32 * np.abs(before).max()
-        compare(got_step, want_step, tol, tie_margin(spec, before))
+        compare(got_step, want_step, tol, step_flip_allowance(spec, before, dt, 3, a, tol))
         t += dt
     got = x.double().cpu().numpy()
     spread = noise_spread(spec, phi0, g32, 1.0, want)
@@ -204,17 +204,20 @@ def test_full_size_step_parity(which):
     got = x.double().cpu().numpy()
     L, _ = oracle.rate(spec, phi0)
     tol = 3 * dt * rate_tol(spec, phi0, L, a) + 8 * U32 * np.abs(phi0).max()
-    ties = tie_margin(spec, phi0) if spec["scheme"] in ("eno2", "eno3") else None
-    compare(got, want, tol, ties)
+    compare(got, want, tol, step_flip_allowance(spec, phi0, dt, 3, a, tol))
 
 
-@pytest.mark.parametrize("tile", [(32, 8, 51, 2), (16, 16, 7, 3), (64, 4, 13, 4),
-                                  (32, 4, 200, 3), (16, 8, 1, 2), (48, 4, 9, 4)])
+@pytest.mark.parametrize("tile", [(32, 8, 51, 2, 0), (16, 16, 7, 3, 0), (64, 4, 13, 4, 0),
+                                  (32, 4, 200, 3, 0), (16, 8, 1, 2, 0), (48, 4, 9, 4, 0),
+                                  (32, 8, 51, 2, 1), (16, 16, 7, 3, 1), (16, 8, 1, 2, 1),
+                                  (32, 4, 200, 4, 1)])
 @pytest.mark.parametrize("scheme", ["weno5", "eno3", "eno2", "upwind1"])
 def test_tiled_kernel_parity_over_tiles(tile, scheme):
     """The tiled 3-D kernel on a ragged air3d grid for several tile shapes
     and chunk lengths (partial tiles on every axis, chunks of one plane and
     longer than the axis), against the oracle."""
+    if tile[4] and scheme != "weno5":
+        pytest.skip("plane pairing is a WENO5 variant")
     spec = W.air3d(nx=[37, 29, 45], scheme=scheme)[0]
     phi = rounded(W.smooth_field(spec, seed=8) + 0.2 * W.rough_field(spec, seed=9), "f32")
     P = B.Problem(spec, check_finite=True)
@@ -225,7 +228,8 @@ def test_tiled_kernel_parity_over_tiles(tile, scheme):
     P.rate(x, out)
     got = out.double().cpu().numpy()
     want, alpha = oracle.rate(spec, phi)
-    compare(got, want, rate_tol(spec, phi, want, alpha), tie_margin(spec, phi))
+    compare(got, want, rate_tol(spec, phi, want, alpha), flip_allowance(spec, phi, alpha),
+            max_frac=0.05)
 
 
 def test_tiled_kernel_parity_4d():
@@ -234,7 +238,7 @@ def test_tiled_kernel_parity_4d():
     spec = W.car4d(n=9, scheme="eno3")[0]
     spec["n"] = [11, 13, 17, 23]
     phi = rounded(W.smooth_field(spec, seed=4) + 0.2 * W.rough_field(spec, seed=5), "f32")
-    for tile in [(16, 8, 5, 2), (32, 4, 13, 3), (32, 8, 2, 4)]:
+    for tile in [(16, 8, 5, 2, 0), (32, 4, 13, 3, 0), (32, 8, 2, 4, 0)]:
         P = B.Problem(spec, check_finite=True)
         P.set_tile(*tile)
         x = to_dev(phi, "f32")
@@ -242,22 +246,23 @@ def test_tiled_kernel_parity_4d():
         P.rate(x, out)
         want, alpha = oracle.rate(spec, phi)
         compare(out.double().cpu().numpy(), want, rate_tol(spec, phi, want, alpha),
-                tie_margin(spec, phi))
+                flip_allowance(spec, phi, alpha), max_frac=0.05)
 
 
 def test_autotune_picks_a_valid_tile_and_keeps_results():
     spec, phi0, g = W.air3d(n=61, t_final=0.2)
     P = B.Problem(spec)
     x = to_dev(phi0, "f32")
-    tb, ta, ch, minb = P.autotune(x)
+    tb, ta, ch, minb, pair = P.autotune(x)
     assert tb > 0 and ta > 0 and ch > 0 and tb * ta <= 256 and minb in (2, 3, 4)
-    assert P.tile() == (tb, ta, ch, minb)
+    assert pair in (0, 1)
+    assert P.tile() == (tb, ta, ch, minb, pair)
     assert torch.equal(x, to_dev(phi0, "f32"))  # autotuning leaves phi alone
     gt = to_dev(g, "f32")
     P.solve(x, gt)
     Q = B.Problem(spec)
-    Q.set_tile(-1, 0, 0, 0)  # generic kernel
-    assert Q.tile() == (-1, -1, -1, -1)
+    Q.set_tile(-1, 0, 0, 0, 0)  # generic kernel
+    assert Q.tile() == (-1, -1, -1, -1, -1)
     y = to_dev(phi0, "f32")
     Q.solve(y, gt)
     assert float((x - y).abs().max()) < 1e-4 * float(y.abs().max())

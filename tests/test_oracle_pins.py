@@ -183,21 +183,22 @@ def test_derivative_is_homogeneous(orc, scheme):
         assert np.abs(pp - lam * pp0).max() < 1e-11 * abs(lam)
 
 
-def test_eno_tie_margin_reported(orc):
-    """The selection margin is 0 at an exact tie between candidates of
-    opposite sign (a step: second differences +1 and -1), 1 where the
-    candidates agree in sign (a parabola: equal second differences) and 1
-    where no choice is made (non-ENO schemes)."""
-    spec = _spec1d(9, "eno2")
+def test_eno_flip_size_reported(orc):
+    """The diagnostic next to ENO derivatives: the change a near-tied
+    selection would cause if taken the other way.  At a step (second
+    differences +1 and -1, an exact tie) it is the jump between the two
+    stencils; on a parabola (equal candidates) it vanishes to rounding; the
+    schemes without selections report 0."""
+    spec = _spec1d(9, "eno2", lo=0.0, hi=8.0)
     step = np.array([0.0, 0.0, 0.0, 0.0, 1.0, 1.0, 1.0, 1.0, 1.0])
-    _, _, tie = orc.derivs(spec, step, 0, with_ties=True)
-    assert tie.min() == 0.0
+    pm, pp, flip = orc.derivs(spec, step, 0, with_ties=True)
+    assert flip.max() == pytest.approx(1.0)  # |S_a - S_b| dx / 2 with S = +-1
     x = W.axis_nodes(spec, 0)
-    _, _, tie = orc.derivs(spec, x ** 2, 0, with_ties=True)
-    assert np.all(tie == 1.0)
+    _, _, flip = orc.derivs(spec, x ** 2, 0, with_ties=True)
+    assert flip.max() < 1e-12
     spec = _spec1d(9, "weno5")
-    _, _, tie = orc.derivs(spec, step, 0, with_ties=True)
-    assert np.all(tie == 1.0)
+    _, _, flip = orc.derivs(spec, step, 0, with_ties=True)
+    assert np.all(flip == 0.0)
 
 
 # --------------------------------------------------------------- Hamiltonians
