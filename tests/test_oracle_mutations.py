@@ -29,10 +29,11 @@ MUTANTS = {
                            "double eps = 1e-6 * sqrt(mx) + 1e-99;"),
     "weno_right_not_mirrored": ("pp[i] = weno5_combine(d[5], d[4], d[3], d[2], d[1]);",
                                 "pp[i] = weno5_combine(d[1], d[2], d[3], d[4], d[5]);"),
-    "eno2_selection_flipped": ("if (fabs(a) <= fabs(b)) {", "if (fabs(a) > fabs(b)) {"),
+    "eno2_selection_flipped": ("int first = force2 < 0 ? (fabs(a) <= fabs(b)) : (force2 == 0);",
+                               "int first = force2 < 0 ? (fabs(a) > fabs(b)) : (force2 == 0);"),
     "eno3_kstar": ("kstar = k - 1;", "kstar = k;"),
-    "eno3_selection_flipped": ("double cs = (fabs(e) <= fabs(f)) ? e : f;",
-                               "double cs = (fabs(e) <= fabs(f)) ? f : e;"),
+    "eno3_selection_flipped": ("int first3 = force3 < 0 ? (fabs(e) <= fabs(f)) : (force3 == 0);",
+                               "int first3 = force3 < 0 ? (fabs(e) > fabs(f)) : (force3 == 0);"),
     "eno2_q2_factor": ("double r = q1 + c * (double)(2 * (i - k) - 1) * dx;",
                        "double r = q1 + c * (double)(2 * (i - k) + 1) * dx;"),
     "second_difference_factor": ("return (D1h(u, j, dx) - D1h(u, j - 1, dx)) / (2.0 * dx);",
