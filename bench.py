@@ -374,7 +374,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 def run_batched(args, rank: int, world: int, local_rank: int):
     """The batched workload: 256 problems (half 2-D normal speed, half 3-D
     air3d, seeded sizes/speeds/radii) in one batched solve per benchmark
-    step; ranks split the problems round-robin by cost (no exchange).  The
+    step; ranks split the problems by estimated cost (sharding.shard, no
+    exchange).  The
     single-problem path (one lsp_hj_solve per problem, in turn) is timed
     beside it on the same problems."""
     import numpy as np
@@ -389,10 +390,10 @@ def run_batched(args, rank: int, world: int, local_rank: int):
         BLD.build()
     if world > 1:
         torch.distributed.barrier()
+    from paper_2411_03501_gb300.sharding import estimated_cost, shard
     allp = W.batched(256)
-    cost = [int(np.prod(sp["n"])) * (1 + i) for i, (sp, _, _) in enumerate(allp)]
-    order = sorted(range(len(allp)), key=lambda i: -cost[i])
-    mine = [allp[i] for k, i in enumerate(order) if k % world == rank]
+    parts = shard([estimated_cost(p[0]) for p in allp], world)
+    mine = [allp[i] for i in parts[rank]]
     specs = [m[0] for m in mine]
     Bt = B.Batch(specs, use_graph=True)
     h_phi0 = [torch.as_tensor(m[1], dtype=torch.float32).pin_memory() for m in mine]
