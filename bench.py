@@ -89,7 +89,8 @@ def algorithmic(spec) -> tuple[float, float]:
     return words * word, float(flops)
 
 
-KERNEL_SOURCES = ["stencil.cuh", "stage_tiled.cuh", "stage_tiled.inl", "stage_generic.cuh"]
+KERNEL_SOURCES = ["stencil.cuh", "stage_tiled.cuh", "stage_tiled.inl", "stage_generic.cuh",
+                  "pair2.cuh", "stage_pair.cuh"]
 
 
 def kernel_hash() -> str:
@@ -395,7 +396,9 @@ def run_batched(args, rank: int, world: int, local_rank: int):
     parts = shard([estimated_cost(p[0]) for p in allp], world)
     mine = [allp[i] for i in parts[rank]]
     specs = [m[0] for m in mine]
-    Bt = B.Batch(specs, use_graph=True)
+    persistent = bool(args.persistent)
+    Bt = B.Batch(specs, use_graph=True, persistent=persistent)
+    Balt = B.Batch(specs, use_graph=True, persistent=not persistent)
     h_phi0 = [torch.as_tensor(m[1], dtype=torch.float32).pin_memory() for m in mine]
     h_g = [torch.as_tensor(m[2], dtype=torch.float32).pin_memory() for m in mine]
     d_phi0 = [t.cuda() for t in h_phi0]
@@ -465,6 +468,22 @@ def run_batched(args, rank: int, world: int, local_rank: int):
     bi = sum(x.numel() * 4 for x in h_phi0) + sum(x.numel() * 4 for x in h_g)
     bo = sum(x.numel() * 4 for x in h_out)
 
+    # the other batched variant (persistent vs stage-synchronous), same timing
+    for _ in range(2):
+        reset()
+        Balt.solve(phis, d_g)
+    torch.cuda.synchronize()
+    alt_ms = 0.0
+    for i in range(args.steps):
+        reset()
+        flush.zero_()
+        ev[i][0].record(stream)
+        Balt.solve(phis, d_g)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    alt_ms = sum(a.elapsed_time(b) for a, b in ev)
+    alt_value = float(units_rank) * args.steps / (alt_ms / 1e3)
+
     # the single-problem path on the same problems, one solve after another
     singles = [B.Problem(sp) for sp in specs]
     reset()
@@ -481,7 +500,8 @@ def run_batched(args, rank: int, world: int, local_rank: int):
     single_value = float(units_rank) / (s0.elapsed_time(s1) / 1e3)
     if rank != 0:
         return 0
-    launches = max(st["steps"] for st in stats) * specs[0]["rk"]  # one launch per stage
+    # one launch per stage, or one cooperative launch per solve
+    launches = 1 if persistent else max(st["steps"] for st in stats) * specs[0]["rk"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -490,7 +510,9 @@ def run_batched(args, rank: int, world: int, local_rank: int):
         "config": {"workload": "batched_256_weno5_rk3_f32", "problems": len(allp),
                    "points": sum(int(np.prod(p[0]["n"])) for p in allp),
                    "parallelism": "problems split across ranks" if world > 1 else "single",
-                   "l2": "flushed (512 MB write) between timed solves", "graph": True,
+                   "l2": "flushed (512 MB write) between timed solves",
+                   "launch": "persistent" if persistent else "stage-synchronous (graph)",
+                   ("stage_synchronous_value" if persistent else "persistent_value"): alt_value,
                    "single_problem_path_value": single_value},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo},
@@ -670,6 +692,9 @@ def main():
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--tile", default="", help="tb,ta,ch,minb: fixed tile instead of autotuning")
     ap.add_argument("--print-kernel-hash", action="store_true")
+    ap.add_argument("--persistent", type=int, default=0,
+                    help="batched workload: time the persistent launch (1) or the "
+                         "stage-synchronous graph (0); the other is timed beside it")
     args = ap.parse_args()
     if args.print_kernel_hash:
         print(kernel_hash())

@@ -22,9 +22,10 @@
  *  - Every call returns an lsp_status and never aborts the process.  The
  *    text of the last error of the calling thread is in lsp_last_error().
  *    Asynchronous CUDA errors surface as LSP_ECUDA on a later call.
- *  - Device-side failures (non-finite values produced) set a flag in the
- *    workspace; they are reported when the call waits for the GPU
- *    (lsp_solve_opts.check_finite) or by lsp_check_status().
+ *  - Device-side failures (non-finite values produced, a bounded wait that
+ *    ran out) set a flag in the workspace; they are reported when the call
+ *    waits for the GPU (lsp_solve_opts.check_finite) or by
+ *    lsp_check_status().  No kernel of the library spins without a limit.
  */
 #ifndef LSP_H
 #define LSP_H
@@ -97,7 +98,14 @@ typedef struct {
                           one graph and launches that                      */
     int batch_chunk;   /* batched solves: planes per CTA along the march of
                           3-D/4-D problems (0 = 32)                        */
-    int reserved[5];   /* must be zero                                     */
+    int batch_persistent; /* batched solves: 1 = the whole solve as ONE
+                          launch of resident CTAs that take (step, stage,
+                          tile) items in order and wait on per-problem
+                          completion counters (use_graph ignored)          */
+    int batch_wait_ms; /* persistent batched solves: limit of one device
+                          wait in milliseconds (0 = 1000); a wait that runs
+                          out ends the launch with LSP_ETIMEOUT            */
+    int reserved[3];   /* must be zero                                     */
 } lsp_solve_opts;
 
 typedef struct {
@@ -191,12 +199,14 @@ lsp_status lsp_hj_solve(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
  * selects the kernel variant compiled for that many CTAs per SM (register
  * budget 128, 80 or 64 per thread); pair = 1 (WENO5 only) selects the variant
  * that carries two consecutive planes per thread through paired FP32
- * instructions.
+ * instructions, pair = 2 the same with the marching axis' WENO5 terms
+ * evaluated once per face (shared by the two nodes of the face; results
+ * identical to pair = 1 bit for bit).
  *  lsp_set_tile(g, 0, 0, 0, 0, 0)   default (32 x 8, chunked for >= 2 waves, 3, 0)
  *  lsp_set_tile(g, -1, 0, 0, 0, 0)  always use the generic kernel
  *  lsp_set_tile(g, tb, ta, ch, minb, pair) explicit; LSP_EINVAL unless
  *        tb*ta <= 256, the haloed tile fits 4 values per thread, the launch
- *        has <= 65535 z-blocks, minb is 2, 3 or 4 and pair is 0 or 1.
+ *        has <= 65535 z-blocks, minb is 2, 3 or 4 and pair is 0, 1 or 2.
  * lsp_get_tile reports the tile a step with `opts` would use (all -1 when
  * the generic kernel runs). */
 lsp_status lsp_set_tile(lsp_grid* grid, int tb, int ta, int ch, int minb, int pair);
@@ -205,7 +215,7 @@ lsp_status lsp_get_tile(const lsp_grid* grid, const lsp_solve_opts* opts, int* t
 
 /* Autotuner: time the first RK stage (phi -> workspace; phi is not
  * modified) for a set of tile shapes, chunk lengths, occupancy targets and,
- * for WENO5, both plane pairings (up to 7 x 7 x 3 x 2 candidates, 3 timed
+ * for WENO5, the three kernel variants (up to 7 x 7 x 3 x 3 candidates, 3 timed
  * launches each) on this grid and
  * keep the fastest in the grid handle (reported through tb/ta/ch/minb/pair, which may
  * be NULL).  Waits for the GPU.  For grids without a tiled kernel it
@@ -253,8 +263,21 @@ lsp_status lsp_hj_solve_noalloc(lsp_grid* grid, const lsp_solve_opts* opts, void
  *  t_final  nprob final times (host)
  *  stats    nprob entries (host, nullable)
  * Workspace: lsp_batched_workspace_size bytes (control block, problem
- * table, CTA table, two stage fields per problem).  Each problem's result
- * equals the single-problem solve of the same grid to FP32 rounding. */
+ * table, CTA table, persistent-launch state, two stage fields per problem).
+ * Each problem's result equals the single-problem solve of the same grid to
+ * FP32 rounding.
+ *
+ * opts->batch_persistent = 1 runs the same stages as ONE cooperative launch
+ * of as many CTAs as fit on the device at once.  The CTAs take work items
+ * (step, stage, tile) from one counter in that order; an item waits until
+ * every tile of the previous stage of its problem has been counted done, so
+ * problems advance independently (a short problem is not held back by the
+ * launch boundaries of a long one) and no host launch separates stages.
+ * Every tile computes exactly what the stage-synchronous launch computes
+ * (identical results bit for bit).  Each wait is bounded by
+ * opts->batch_wait_ms; one that runs out raises LSP_ETIMEOUT (reported as
+ * described for check_finite), makes the other CTAs stop at their next item
+ * and leaves the fields partly advanced; the CUDA context stays usable. */
 lsp_status lsp_batched_workspace_size(int nprob, lsp_grid* const* grids,
                                       const lsp_solve_opts* opts, size_t* bytes);
 lsp_status lsp_hj_solve_batched(int nprob, lsp_grid* const* grids, const lsp_solve_opts* opts,
@@ -307,8 +330,16 @@ lsp_status lsp_loss_tube(const lsp_grid* grid, int dtype, const void* phi, const
 
 /* Wait for `stream` and report a device-side failure flagged in the
  * workspace control block since the last call that reset it (every step
- * and solve resets it on entry).  LSP_OK, LSP_ENONFINITE or LSP_ECUDA. */
+ * and solve resets it on entry).  LSP_OK, LSP_ETIMEOUT (takes precedence),
+ * LSP_ENONFINITE or LSP_ECUDA. */
 lsp_status lsp_check_status(const void* workspace, void* stream);
+
+/* Testing aid for the bounded waits of the persistent batched launch: from
+ * now on the tiles of problem `problem` (index into the caller's arrays) are
+ * never counted done, so the first wait on that problem runs out and the
+ * solve reports LSP_ETIMEOUT.  -1 switches it off.  Returns the previous
+ * setting.  Process-wide; not for production use. */
+int lsp_debug_stall_problem(int problem);
 
 /* Text for a status code; thread-local text of the last error. */
 const char* lsp_status_string(lsp_status s);

@@ -27,7 +27,7 @@ EXPORTS = [
     "lsp_hj_step", "lsp_hj_solve", "lsp_check_status", "lsp_hj_solve_noalloc",
     "lsp_set_tile", "lsp_get_tile", "lsp_autotune", "lsp_batched_workspace_size",
     "lsp_hj_solve_batched", "lsp_adjoint_workspace_size", "lsp_hj_solve_ckpt", "lsp_hj_adjoint",
-    "lsp_loss_tube",
+    "lsp_loss_tube", "lsp_debug_stall_problem",
 ]
 
 
@@ -47,7 +47,9 @@ class lsp_solve_opts(ctypes.Structure):
         ("check_finite", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("batch_chunk", ctypes.c_int),
-        ("reserved", ctypes.c_int * 5),
+        ("batch_persistent", ctypes.c_int),
+        ("batch_wait_ms", ctypes.c_int),
+        ("reserved", ctypes.c_int * 3),
     ]
 
 
@@ -94,6 +96,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.lsp_hj_solve.argtypes = [vp, op, vp, vp, ctypes.c_double, ctypes.c_double, vp, sz,
                                ctypes.POINTER(lsp_solve_stats), vp]
     L.lsp_check_status.argtypes = [vp, vp]
+    L.lsp_debug_stall_problem.argtypes = [ctypes.c_int]
+    L.lsp_debug_stall_problem.restype = ctypes.c_int
     L.lsp_hj_solve_noalloc.argtypes = [vp, op, vp, vp, ctypes.c_double, ctypes.c_double,
                                        ctypes.POINTER(lsp_solve_stats), vp]
     ip = ctypes.POINTER(ctypes.c_int)
@@ -312,7 +316,8 @@ class Batch:
     """Batched solve of several problem descriptions (dicts of
     :mod:`workloads`) sharing scheme, RK order, CFL and tube."""
 
-    def __init__(self, specs, device="cuda", check_finite=False, use_graph=True, chunk=0):
+    def __init__(self, specs, device="cuda", check_finite=False, use_graph=True, chunk=0,
+                 persistent=False, wait_ms=0):
         import torch
         self.specs = specs
         self.grids = []
@@ -325,6 +330,8 @@ class Batch:
         self.opts = make_opts(s0.get("rk", 3), s0["scheme"], "f32", s0.get("tube", False),
                               s0.get("cfl", 0.75), check_finite, use_graph)
         self.opts.batch_chunk = int(chunk)
+        self.opts.batch_persistent = 1 if persistent else 0
+        self.opts.batch_wait_ms = int(wait_ms)
         nbytes = lsp_batched_workspace_size(self.grids, self.opts)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
 
@@ -336,6 +343,12 @@ class Batch:
 
 def lsp_check_status(workspace, stream=None):
     _check(load().lsp_check_status(_ptr(workspace), _stream(stream)))
+
+
+def lsp_debug_stall_problem(problem: int) -> int:
+    """Testing aid: the persistent batched launch never counts problem
+    `problem` done (-1: off), so its bounded waits run out."""
+    return int(load().lsp_debug_stall_problem(int(problem)))
 
 
 # ----------------------------------------------------------------- helpers

@@ -20,4 +20,21 @@ struct BatchProblem {
 
 constexpr int kBatchTB = 32, kBatchTA = 8;
 
+// Persistent batched launch: work items (step k, stage s, tile b) are handed
+// out in this order by one counter; the steps split into segments with a
+// constant set of active problems (a prefix of the table).
+struct BatchSegment {
+    long long item_start;  // first item of the segment
+    int k_start;           // first step of the segment
+    int blocks;            // CTAs per stage in the segment
+};
+
+struct PersistCtl {
+    unsigned long long next;  // next work item
+    unsigned int abort;       // set once a CTA gave up waiting
+    int stall_problem;        // test hook: this problem never reports done (-1: none)
+    unsigned long long pad[30];
+};
+static_assert(sizeof(PersistCtl) <= 256, "persistent control block must fit 256 bytes");
+
 }  // namespace lsp

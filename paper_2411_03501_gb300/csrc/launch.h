@@ -31,8 +31,15 @@ bool tile_valid(int ndim, int scheme, const Tile& t, const int* n);
 
 // Batched stages (batched.cu): RK2/RK3, FP32, problems of 2 to 4 dimensions.
 struct BatchProblem;
+struct BatchSegment;
+struct PersistCtl;
 cudaError_t launch_batched(int scheme, const BatchProblem* probs, const int* block_prob, int nblocks,
                            int step, int stage, int rk, cudaStream_t s);
+// The whole batched solve as one cooperative launch of resident CTAs.
+cudaError_t launch_batched_persistent(int scheme, const BatchProblem* probs, const int* block_prob,
+                                      const BatchSegment* segs, int nseg, int rk,
+                                      unsigned int* done, PersistCtl* pc, Ctl* ctl,
+                                      unsigned long long wait_ns, cudaStream_t s);
 void batch_tile_dims(int* tb, int* ta);
 bool batch_supported(int ndim, int dyn);
 

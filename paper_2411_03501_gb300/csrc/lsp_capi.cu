@@ -82,9 +82,12 @@ lsp_status check_opts(const lsp_grid* g, const lsp_solve_opts* o)
     if (o->scheme < LSP_UPWIND1 || o->scheme > LSP_WENO5) return fail(LSP_EINVAL, "bad scheme");
     if (o->dtype != LSP_F32 && o->dtype != LSP_F64) return fail(LSP_EINVAL, "bad dtype");
     if (!(o->cfl > 0.0 && o->cfl <= 1.0)) return fail(LSP_EINVAL, "cfl must be in (0, 1]");
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 3; ++i)
         if (o->reserved[i]) return fail(LSP_EINVAL, "reserved option fields must be zero");
     if (o->batch_chunk < 0) return fail(LSP_EINVAL, "batch_chunk must be >= 0");
+    if (o->batch_persistent != 0 && o->batch_persistent != 1)
+        return fail(LSP_EINVAL, "batch_persistent must be 0 or 1");
+    if (o->batch_wait_ms < 0) return fail(LSP_EINVAL, "batch_wait_ms must be >= 0");
     const int G = lsp::ghost_width(o->scheme);
     for (int k = 0; k < g->ndim; ++k)
         if (g->n[k] < 2 * G + 1)
@@ -295,6 +298,8 @@ lsp_status read_flags(const void* ws, cudaStream_t st)
     if (e) return cuda_fail(e, "read flags");
     e = cudaStreamSynchronize(st);
     if (e) return cuda_fail(e, "synchronize");
+    if (f & lsp::kFlagTimeout)
+        return fail(LSP_ETIMEOUT, "a device-side wait ran out; the results are incomplete");
     if (f & lsp::kFlagNonFinite) return fail(LSP_ENONFINITE, "a non-finite value was produced");
     return LSP_OK;
 }
@@ -697,7 +702,7 @@ lsp_status lsp_autotune(lsp_grid* g, const lsp_solve_opts* o, const void* phi, v
     lsp::Tile best{0, 0, 0, 0, 0};
     const double dt = cfl_dt_host(g, o->cfl, 0.0, INFINITY);
     for (const auto& sh : shapes) {
-        for (int cand = 0; cand < 42; ++cand) {
+        for (int cand = 0; cand < 63; ++cand) {
             const int sp = splits[cand % 7];
             const int minb = 2 + (cand / 7) % 3;
             const int pair = cand / 21;
@@ -786,6 +791,17 @@ lsp_status batch_check(int nprob, lsp_grid* const* grids, const lsp_solve_opts* 
     return LSP_OK;
 }
 
+// Persistent launch state: control block, per-problem completion counters,
+// segment table (at most one segment per problem, plus the end marker).
+size_t batch_persist_bytes(int nprob)
+{
+    return round256(sizeof(lsp::PersistCtl)) + round256((size_t)nprob * sizeof(unsigned int)) +
+           round256((size_t)(nprob + 1) * sizeof(lsp::BatchSegment));
+}
+
+// Test hook of the persistent batched launch (lsp_debug_stall_problem).
+int g_stall_problem = -1;
+
 // Tile grid and field sizes of every problem; the total workspace bytes.
 void batch_geometry(int nprob, lsp_grid* const* grids, const lsp_solve_opts* o,
                     std::vector<BatchPlanEntry>& plan, size_t* bytes, long long* total_blocks)
@@ -820,12 +836,80 @@ void batch_geometry(int nprob, lsp_grid* const* grids, const lsp_solve_opts* o,
     }
     *total_blocks = blocks;
     *bytes = lsp::kCtlBytes + round256((size_t)nprob * sizeof(lsp::BatchProblem)) +
-             round256((size_t)blocks * sizeof(int)) + fields;
+             round256((size_t)blocks * sizeof(int)) + batch_persist_bytes(nprob) + fields;
+}
+
+// The persistent variant of lsp_hj_solve_batched: segments of steps with a
+// constant set of active problems (a prefix of `order`, sorted by decreasing
+// step count), items (step, stage, tile) numbered in that order, one
+// cooperative launch.
+lsp_status solve_batched_persistent(int nprob, const lsp_solve_opts* o,
+                                    const std::vector<BatchPlanEntry>& order,
+                                    const std::vector<int>& prefix, const lsp::BatchProblem* d_table,
+                                    const int* d_block_prob, lsp::PersistCtl* d_pc,
+                                    unsigned int* d_done, lsp::BatchSegment* d_segs, lsp::Ctl* ctl,
+                                    void* ws, cudaStream_t st)
+{
+    const int rk = o->rk_order;
+    std::vector<lsp::BatchSegment> segs;
+    long long items = 0;
+    int nactive = nprob, k = 0;
+    for (;;) {
+        while (nactive > 0 && order[nactive - 1].nsteps <= k) --nactive;
+        if (nactive == 0) break;
+        const int k_end = order[nactive - 1].nsteps;
+        lsp::BatchSegment sg;
+        sg.item_start = items;
+        sg.k_start = k;
+        sg.blocks = prefix[nactive];
+        segs.push_back(sg);
+        items += (long long)(k_end - k) * rk * prefix[nactive];
+        k = k_end;
+    }
+    for (int j = 0; j < nprob; ++j)
+        if ((long long)order[j].nsteps * rk * order[j].nblocks > 0xffffffffLL)
+            return fail(LSP_EINVAL, "problem %d: too many tile stages for one persistent launch",
+                        order[j].p);
+    const int nseg = (int)segs.size();
+    lsp::BatchSegment end;
+    end.item_start = items;
+    end.k_start = k;
+    end.blocks = 0;
+    segs.push_back(end);
+
+    lsp::PersistCtl pc;
+    std::memset(&pc, 0, sizeof(pc));
+    pc.stall_problem = -1;
+    for (int j = 0; j < nprob; ++j)
+        if (order[j].p == g_stall_problem) pc.stall_problem = j;
+
+    lsp_status s = reset_flags(ws, st);
+    if (s) return s;
+    // pageable sources: the copies are staged before the calls return
+    cudaError_t e = cudaMemcpyAsync(d_pc, &pc, sizeof(pc), cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(segs[0]),
+                                cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemsetAsync(d_done, 0, (size_t)nprob * sizeof(unsigned int), st);
+    if (e) return cuda_fail(e, "upload persistent state");
+    if (items == 0) return LSP_OK;
+    const unsigned long long wait_ns =
+        (unsigned long long)(o->batch_wait_ms > 0 ? o->batch_wait_ms : 1000) * 1000000ULL;
+    e = lsp::launch_batched_persistent(o->scheme, d_table, d_block_prob, d_segs, nseg, rk, d_done,
+                                       d_pc, ctl, wait_ns, st);
+    if (e) return cuda_fail(e, "persistent batched kernel");
+    return LSP_OK;
 }
 
 }  // namespace
 
 extern "C" {
+
+int lsp_debug_stall_problem(int problem)
+{
+    const int prev = g_stall_problem;
+    g_stall_problem = problem;
+    return prev;
+}
 
 lsp_status lsp_batched_workspace_size(int nprob, lsp_grid* const* grids, const lsp_solve_opts* o,
                                       size_t* bytes)
@@ -895,6 +979,12 @@ lsp_status lsp_hj_solve_batched(int nprob, lsp_grid* const* grids, const lsp_sol
     base += round256((size_t)nprob * sizeof(lsp::BatchProblem));
     int* d_block_prob = (int*)base;
     base += round256((size_t)total_blocks * sizeof(int));
+    lsp::PersistCtl* d_pc = (lsp::PersistCtl*)base;
+    base += round256(sizeof(lsp::PersistCtl));
+    unsigned int* d_done = (unsigned int*)base;
+    base += round256((size_t)nprob * sizeof(unsigned int));
+    lsp::BatchSegment* d_segs = (lsp::BatchSegment*)base;
+    base += round256((size_t)(nprob + 1) * sizeof(lsp::BatchSegment));
 
     std::vector<lsp::BatchProblem> table(nprob);
     std::vector<int> block_prob((size_t)total_blocks);
@@ -933,6 +1023,14 @@ lsp_status lsp_hj_solve_batched(int nprob, lsp_grid* const* grids, const lsp_sol
     if (!e) e = cudaMemcpyAsync(d_block_prob, block_prob.data(), block_prob.size() * sizeof(int),
                                 cudaMemcpyHostToDevice, st);
     if (e) return cuda_fail(e, "upload batch table");
+
+    if (o->batch_persistent) {
+        s = solve_batched_persistent(nprob, o, order, prefix, d_table, d_block_prob, d_pc, d_done,
+                                     d_segs, ctl, ws, st);
+        if (s) return s;
+        if (o->check_finite) return read_flags(ws, st);
+        return LSP_OK;
+    }
 
     cudaStream_t es = st;
     cudaStream_t cap = nullptr;

@@ -27,6 +27,7 @@ struct Ctl {
 static_assert(sizeof(Ctl) <= 256, "control block must fit 256 bytes");
 constexpr size_t kCtlBytes = 256;
 constexpr unsigned int kFlagNonFinite = 1u;
+constexpr unsigned int kFlagTimeout = 2u;
 
 // Arguments of one fused stage launch.  Every launch computes, at every node,
 //   out = c_n * phi_n + c_s * phi_s + c_l * dt * L(phi_s)

@@ -76,4 +76,52 @@ __device__ __forceinline__ void deriv_weno5_jp2(const F2* u, float inv_dx, float
     pp = (cen + weno_phi2(is0p, is1p, is2p, eR, T1, T0)) * F2(inv_dx);
 }
 
+// The two WENO5 corrections that share the face between nodes j and j+1,
+// from the six values v[o] = phi_{j-2+o}: phim for the left-biased
+// derivative at node j+1 and phip for the right-biased derivative at node j.
+// Both sides of a face see the same five first differences, so their
+// smoothness indicators are the same three numbers in reversed order and
+// their regulariser is the same; everything up to the squared scaled
+// indicators is computed once.  Each result is bit-identical to the
+// corresponding weno_phi2 call of deriv_weno5_jp2 (the same operations on the
+// same operands: negated FMAs round symmetrically, products commute, and the
+// scaling by an exact power of two commutes with rounding, so
+// fma(is, sc, e*sc) == (is + e) * sc).  cen receives the centred term of
+// node j (x: (7 (d_{j-1} + d_j) - (d_{j-2} + d_{j+1})) / 12).
+__device__ __forceinline__ void weno5_face2(const F2* v, float floor12, F2& phim, F2& phip,
+                                            F2& cen_j)
+{
+    const F2 da = v[1] - v[0], db = v[2] - v[1], dc = v[3] - v[2];
+    const F2 dd = v[4] - v[3], de = v[5] - v[4];
+    cen_j = (fma2(F2(7.0f), db + dc, -(da + dd))) * F2(1.0f / 12.0f);
+    // second differences S_{j-1} .. S_{j+2}
+    const F2 Sa = db - da, Sb = dc - db, Sc = dd - dc, Sd = de - dd;
+    const F2 m4 = max2(max2(db * db, dc * dc), max2(dd * dd, de * de));
+    const F2 e = fma2(F2(1.2e-5f), max2(m4, da * da), F2(floor12));
+    const F2 g1 = Sa - Sb, g2 = Sb - Sc, g3 = Sc - Sd;
+    const F2 e1 = g1 * g1, e2 = g2 * g2, e3 = g3 * g3;
+    const F2 f0 = fma2(F2(-3.0f), Sb, Sa), f1 = Sb + Sc, f2 = fma2(F2(3.0f), Sc, -Sd);
+    const F2 three(3.0f), thirteen(13.0f), two(2.0f);
+    const F2 b0 = fma2(thirteen, e1, three * f0 * f0);
+    const F2 b1 = fma2(thirteen, e2, three * f1 * f1);
+    const F2 b2 = fma2(thirteen, e3, three * f2 * f2);
+    const F2 Tj = fma2(-two, Sb, Sa + Sc), Tj1 = fma2(-two, Sc, Sb + Sd);
+    const F2 sc(__uint_as_float(0x7f000000u - (__float_as_uint(e.v.x) & 0x7f800000u)),
+                __uint_as_float(0x7f000000u - (__float_as_uint(e.v.y) & 0x7f800000u)));
+    const F2 esc = e * sc;
+    const F2 q0 = fma2(b0, sc, esc), q1 = fma2(b1, sc, esc), q2 = fma2(b2, sc, esc);
+    const F2 Q0 = q0 * q0, Q1 = q1 * q1, Q2 = q2 * q2;
+    const F2 Q12 = Q1 * Q2, Q01 = Q0 * Q1;
+    // left-biased side of node j+1: indicators (b0, b1, b2), A = T_j, B = T_{j+1}
+    const F2 Pm = fma2(F2(6.0f) * Q0, Q2, fma2(three, Q01, Q12));
+    const F2 rm(__fdividef(1.0f, Pm.v.x), __fdividef(1.0f, Pm.v.y));
+    const F2 w0m = Q12 * rm, w2m = three * Q01 * rm;
+    phim = fma2(w0m * F2(1.0f / 3.0f), Tj, (w2m - F2(0.5f)) * (Tj1 * F2(1.0f / 6.0f)));
+    // right-biased side of node j: indicators (b2, b1, b0), A = T_{j+1}, B = T_j
+    const F2 Pp = fma2(F2(6.0f) * Q2, Q0, fma2(three, Q12, Q01));
+    const F2 rp(__fdividef(1.0f, Pp.v.x), __fdividef(1.0f, Pp.v.y));
+    const F2 w0p = Q01 * rp, w2p = three * Q12 * rp;
+    phip = fma2(w0p * F2(1.0f / 3.0f), Tj1, (w2p - F2(0.5f)) * (Tj * F2(1.0f / 6.0f)));
+}
+
 }  // namespace lsp

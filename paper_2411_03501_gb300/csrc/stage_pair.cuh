@@ -45,7 +45,11 @@ __device__ __forceinline__ F2 hamiltonian_pair(const F2* x, const F2* p, const f
     }
 }
 
-template <int NDIM, int DYN>
+// FACES = true: the marching axis' derivatives come from shared faces
+// (weno5_face2): one face evaluation per node instead of two one-sided ones,
+// the left-biased correction of the next plane carried in a register.  The
+// results are bit-identical to FACES = false.
+template <int NDIM, int DYN, bool FACES = false>
 __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int TB, int TA, int bx,
                                                 int by, int chunk, int outer, int ch, float* tile,
                                                 int tx, int ty)
@@ -125,6 +129,16 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
     fetch(min(s_begin + 1, nS - 1), pfB);
     float wnA = line_value(col, s_begin + G, nS, sS, a.periodic[AS]);
     float wnB = line_value(col, s_begin + G + 1, nS, sS, a.periodic[AS]);
+    // FACES: left-biased correction of node s from the face s - 1/2 (values
+    // s-3 .. s+2 = w[0..5] at the start of the chunk)
+    float phim_next = 0.f;
+    if constexpr (FACES) {
+        F2 v[6], fm, fp, c;
+#pragma unroll
+        for (int o = 0; o < 6; ++o) v[o] = F2(w[o]);
+        weno5_face2(v, fl_s, fm, fp, c);
+        phim_next = fm.x();
+    }
 
     for (int s = s_begin; s < s_end; s += 2) {
         float* curA = tile + (((s - s_begin) >> 1) & 1) * (2 * HW);
@@ -147,9 +161,21 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
         if (active) {
             const bool second = s + 1 < s_end;
             F2 u[2 * G + 1], pm, pp, pbar[NDIM], diss(0.f);
+            if constexpr (FACES) {
+                // faces s + 1/2 (x) and s + 3/2 (y): values w[1..6] and w[2..7]
+                F2 fm, fp, c;
 #pragma unroll
-            for (int o = 0; o <= 2 * G; ++o) u[o] = F2(w[o], w[o + 1]);
-            deriv_weno5_jp2(u, a.inv_dx[AS], fl_s, pm, pp);
+                for (int o = 0; o < 6; ++o) u[o] = F2(w[o + 1], w[o + 2]);
+                weno5_face2(u, fl_s, fm, fp, c);
+                const F2 sx(a.inv_dx[AS]);
+                pm = (c - F2(phim_next, fm.x())) * sx;
+                pp = (c + fp) * sx;
+                phim_next = fm.y();
+            } else {
+#pragma unroll
+                for (int o = 0; o <= 2 * G; ++o) u[o] = F2(w[o], w[o + 1]);
+                deriv_weno5_jp2(u, a.inv_dx[AS], fl_s, pm, pp);
+            }
             pbar[AS] = F2(0.5f) * (pp + pm);
             diss = F2(0.5f * alpha[AS]) * (pp - pm);
 #pragma unroll
@@ -196,12 +222,12 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
 
 // Single-problem launch of the paired body (WENO5, FP32): blockDim = (tb,
 // ta); gridDim = (ceil(nB/tb), ceil(nA/ta), nchunks * nOuter); ch is even.
-template <int NDIM, int DYN, int MINB>
+template <int NDIM, int DYN, int MINB, bool FACES>
 __global__ void __launch_bounds__(256, MINB) stage_pair_kernel(StageArgs<float> a, int ch, int nchunks)
 {
     extern __shared__ unsigned char smem_raw[];
     float* tile = reinterpret_cast<float*>(smem_raw);
-    tiled_pair_body<NDIM, DYN>(a, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y,
+    tiled_pair_body<NDIM, DYN, FACES>(a, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y,
                                blockIdx.z % nchunks, blockIdx.z / nchunks, ch, tile, threadIdx.x,
                                threadIdx.y);
 }

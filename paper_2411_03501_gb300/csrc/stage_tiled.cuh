@@ -96,18 +96,29 @@ __device__ __forceinline__ void deriv_fast(const R* u, R inv_dx, R floor12, R& p
     else deriv<SCHEME>(u, inv_dx, pm, pp);
 }
 
+// Loads of the stage input.  COH = false: through the read-only cache (the
+// field does not change during the launch).  COH = true: from L2, bypassing
+// L1 -- for the persistent batched launch, in which other CTAs of the same
+// launch write the fields a CTA reads later.
+template <bool COH, typename R>
+__device__ __forceinline__ R ld_in(const R* p)
+{
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+}
+
 // Value at index j of a line of n nodes whose node 0 is at p[0] with stride
 // s, ghost cells substituted (periodic wrap or linear extrapolation).
-template <typename R>
+template <typename R, bool COH = false>
 __device__ __forceinline__ R line_value(const R* __restrict__ p, int j, int n, int s, int periodic)
 {
-    if (j >= 0 && j < n) return __ldg(p + j * s);
-    if (periodic) return __ldg(p + (j < 0 ? j + n : j - n) * s);
+    if (j >= 0 && j < n) return ld_in<COH>(p + j * s);
+    if (periodic) return ld_in<COH>(p + (j < 0 ? j + n : j - n) * s);
     if (j < 0) {
-        const R u0 = __ldg(p), u1 = __ldg(p + s);
+        const R u0 = ld_in<COH>(p), u1 = ld_in<COH>(p + s);
         return u0 + R(-j) * (u0 - u1);
     }
-    const R un = __ldg(p + (n - 1) * s), um = __ldg(p + (n - 2) * s);
+    const R un = ld_in<COH>(p + (n - 1) * s), um = ld_in<COH>(p + (n - 2) * s);
     return un + R(j - n + 1) * (un - um);
 }
 
@@ -121,7 +132,7 @@ struct Tile {
 // chunk `chunk` of the march along axis S and, for 4-D grids, index `outer`
 // along axis 0.  2-D grids have no march (one plane).  Block of TB x TA
 // threads (tx, ty); `tile` holds (TA + 2G) x (TB + 2G) values.
-template <int NDIM, int SCHEME, int DYN, typename R>
+template <int NDIM, int SCHEME, int DYN, typename R, bool COH = false>
 __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, int TA, int bx,
                                                  int by, int chunk, int outer, int ch, R* tile,
                                                  int tx, int ty)
@@ -170,7 +181,7 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
     if constexpr (HAS_S) {
 #pragma unroll
         for (int o = -G; o < G; ++o)
-            w[o + G] = line_value(col, s_begin + o, nS, sS, a.periodic[AS]);
+            w[o + G] = line_value<R, COH>(col, s_begin + o, nS, sS, a.periodic[AS]);
     }
 
     // This thread's share of the plane tile (with halo): at most 4 slots.
@@ -197,14 +208,14 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
             const unsigned kind = (kinds >> (2 * k)) & 3u;
             R v = R(0);
             if (kind == 0u) {
-                v = __ldg(plane + e_off[k]);
+                v = ld_in<COH>(plane + e_off[k]);
             } else if (kind == 1u) {  // e_off = ja; jb recomputed from the slot
                 const int e = tid + k * nthr;
-                v = line_value(plane + e_off[k] * sA, b0 - G + (e - (e / W) * W), nB, 1,
+                v = line_value<R, COH>(plane + e_off[k] * sA, b0 - G + (e - (e / W) * W), nB, 1,
                                a.periodic[AB]);
             } else if (kind == 2u) {  // e_off = jb
                 const int e = tid + k * nthr;
-                v = line_value(plane + e_off[k], a0 - G + e / W, nA, sA, a.periodic[AA]);
+                v = line_value<R, COH>(plane + e_off[k], a0 - G + e / W, nA, sA, a.periodic[AA]);
             }
             pf[k] = v;
         }
@@ -212,7 +223,7 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
     R pf[MAXE];
     fetch(s_begin, pf);
     R wnext = R(0);
-    if constexpr (HAS_S) wnext = line_value(col, s_begin + G, nS, sS, a.periodic[AS]);
+    if constexpr (HAS_S) wnext = line_value<R, COH>(col, s_begin + G, nS, sS, a.periodic[AS]);
 
     for (int s = s_begin; s < s_end; ++s) {
         R* cur = tile + ((s - s_begin) & 1) * (H * W);  // double buffer
@@ -223,7 +234,7 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
         __syncthreads();  // plane s staged; the other buffer is free
         if (s + 1 < s_end) {  // issue plane s+1's loads before computing plane s
             fetch(s + 1, pf);
-            if constexpr (HAS_S) wnext = line_value(col, s + 1 + G, nS, sS, a.periodic[AS]);
+            if constexpr (HAS_S) wnext = line_value<R, COH>(col, s + 1 + G, nS, sS, a.periodic[AS]);
         }
         const R* tile_s = cur;
         __syncthreads();
@@ -259,7 +270,7 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
                 const R* col0 = a.phi_s + s * sS + ia * sA + ib;
 #pragma unroll
                 for (int o = -G; o <= G; ++o)
-                    u[o + G] = line_value(col0, outer + o, a.n[0], a.stride[0], a.periodic[0]);
+                    u[o + G] = line_value<R, COH>(col0, outer + o, a.n[0], a.stride[0], a.periodic[0]);
                 deriv_fast<SCHEME>(u, a.inv_dx[0], weno_floor12(a.inv_dx[0]), pm, pp);
                 pbar[0] = R(0.5) * (pp + pm);
                 diss += alpha[0] * R(0.5) * (pp - pm);
@@ -269,7 +280,7 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
             const R L = -(Hv - diss);
             const int idx = base_outer + s * sS + ia * sA + ib;
             R v = a.c_s * center + cl * L;
-            if (a.phi_n) v += a.c_n * a.phi_n[idx];
+            if (a.phi_n) v += a.c_n * (COH ? __ldcg(a.phi_n + idx) : a.phi_n[idx]);
             if (a.tube) v = rmin(v, __ldg(a.target + idx));
             if (!isfinite(v)) atomicOr(&a.ctl->flags, kFlagNonFinite);
             a.out[idx] = v;

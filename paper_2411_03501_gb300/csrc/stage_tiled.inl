@@ -17,8 +17,12 @@ static cudaError_t tiled_one(const StageArgs<float>& a, const Tile& t, cudaStrea
               nchunks * (NDIM == 4 ? a.n[0] : 1));
     const size_t smem = 2 * sizeof(float) * (t.ta + 2 * G) * (t.tb + 2 * G);
     if constexpr (SCHEME == WENO5) {
-        if (t.pair) {
-            stage_pair_kernel<NDIM, DYN, LSP_MINB><<<grid, block, 2 * smem, s>>>(a, t.ch, nchunks);
+        if (t.pair == 1) {
+            stage_pair_kernel<NDIM, DYN, LSP_MINB, false><<<grid, block, 2 * smem, s>>>(a, t.ch, nchunks);
+            return cudaGetLastError();
+        }
+        if (t.pair == 2) {
+            stage_pair_kernel<NDIM, DYN, LSP_MINB, true><<<grid, block, 2 * smem, s>>>(a, t.ch, nchunks);
             return cudaGetLastError();
         }
     }

@@ -96,3 +96,66 @@ def test_batched_rejections():
     with pytest.raises(B.LspError) as e:
         B.lsp_batched_workspace_size(Bt.grids, o)
     assert e.value.status == B.LSP_EUNSUPPORTED
+
+
+def _mixed_with_4d(scheme, rk, seed=11):
+    specs, phis, gs = _mixed(count=8, seed=seed)
+    sp, phi, g = W.car4d(n=12, t_final=0.4)
+    specs.append(sp)
+    phis.append(rounded(phi, "f32"))
+    gs.append(rounded(g, "f32"))
+    for s in specs:
+        s["scheme"] = scheme
+        s["rk"] = rk
+    return specs, phis, gs
+
+
+@pytest.mark.parametrize("scheme,rk", [("weno5", 3), ("eno2", 2), ("eno3", 3)])
+def test_persistent_equals_stage_synchronous(scheme, rk):
+    """The persistent launch (one cooperative launch, work items taken in
+    (step, stage, tile) order, per-problem completion counters) runs the same
+    tile computations as the stage-synchronous launches: identical fields
+    bit for bit, for 2-D, 3-D and 4-D problems with uneven horizons (one of
+    them zero)."""
+    specs, phis, gs = _mixed_with_4d(scheme, rk)
+    tf = [s["t_final"] * f for s, f in zip(specs, [1.0, 0.0, 0.5, 1.0, 0.2, 1.0, 0.7, 1.0, 1.0])]
+    gts = [to_dev(g, "f32") for g in gs]
+    ref = [to_dev(p, "f32") for p in phis]
+    st_ref = B.Batch(specs, check_finite=True).solve(ref, gts, t_final=tf)
+    got = [to_dev(p, "f32") for p in phis]
+    st_got = B.Batch(specs, check_finite=True, persistent=True).solve(got, gts, t_final=tf)
+    torch.cuda.synchronize()
+    assert st_got == st_ref
+    assert st_got[1]["steps"] == 0
+    for i in range(len(specs)):
+        assert torch.equal(got[i], ref[i]), (i, float((got[i] - ref[i]).abs().max()))
+
+
+def test_persistent_wait_runs_out_and_context_survives():
+    """A problem whose tiles are never counted done (the library's testing
+    hook) makes the first wait on it run out: the launch ends, the solve
+    reports LSP_ETIMEOUT (directly with check_finite, else through
+    lsp_check_status), and the context stays usable -- the next solve on the
+    same workspace succeeds and matches the stage-synchronous result."""
+    specs, phis, gs = _mixed(count=4, seed=3)
+    gts = [to_dev(g, "f32") for g in gs]
+    Bt = B.Batch(specs, check_finite=True, persistent=True, wait_ms=50)
+    Bq = B.Batch(specs, check_finite=False, persistent=True, wait_ms=50)
+    prev = B.lsp_debug_stall_problem(1)
+    try:
+        with pytest.raises(B.LspError) as e:
+            Bt.solve([to_dev(p, "f32") for p in phis], gts)
+        assert e.value.status == B.LSP_ETIMEOUT
+        Bq.solve([to_dev(p, "f32") for p in phis], gts)
+        with pytest.raises(B.LspError) as e:
+            B.lsp_check_status(Bq.workspace)
+        assert e.value.status == B.LSP_ETIMEOUT
+    finally:
+        B.lsp_debug_stall_problem(prev)
+    got = [to_dev(p, "f32") for p in phis]
+    Bt.solve(got, gts)
+    ref = [to_dev(p, "f32") for p in phis]
+    B.Batch(specs).solve(ref, gts)
+    torch.cuda.synchronize()
+    for i in range(len(specs)):
+        assert torch.equal(got[i], ref[i]), i
