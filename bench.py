@@ -44,10 +44,12 @@ def _peaks():
 
 def workload(name: str):
     from paper_2411_03501_gb300 import workloads as W
-    if name == "air3d_201":
-        spec, phi0, g = W.air3d(n=201)
-    elif name == "car4d_81":
-        spec, phi0, g = W.car4d(n=81)
+    # air3d_<n>, car4d_<n>: the game workloads at n nodes per axis (the
+    # benchmark lines use 201 and 81; smaller n serve profiler captures)
+    if name.startswith("air3d_") and name[6:].isdigit():
+        spec, phi0, g = W.air3d(n=int(name[6:]))
+    elif name.startswith("car4d_") and name[6:].isdigit():
+        spec, phi0, g = W.car4d(n=int(name[6:]))
     elif name == "normal_speed_2d":
         spec, phi0, g = W.normal_speed_2d(101)
     else:

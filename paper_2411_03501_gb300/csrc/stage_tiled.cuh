@@ -226,18 +226,19 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
     if constexpr (HAS_S) wnext = line_value<R, COH>(col, s_begin + G, nS, sS, a.periodic[AS]);
 
     for (int s = s_begin; s < s_end; ++s) {
-        R* cur = tile + ((s - s_begin) & 1) * (H * W);  // double buffer
+        // double buffer: the buffer written here was last read two planes
+        // ago, before every thread passed the previous plane's barrier
+        R* cur = tile + ((s - s_begin) & 1) * (H * W);
 #pragma unroll
         for (int k = 0; k < MAXE; ++k)
             if (((kinds >> (2 * k)) & 3u) != 3u) cur[tid + k * nthr] = pf[k];
         if constexpr (HAS_S) w[2 * G] = wnext;
-        __syncthreads();  // plane s staged; the other buffer is free
+        __syncthreads();  // plane s staged
         if (s + 1 < s_end) {  // issue plane s+1's loads before computing plane s
             fetch(s + 1, pf);
             if constexpr (HAS_S) wnext = line_value<R, COH>(col, s + 1 + G, nS, sS, a.periodic[AS]);
         }
         const R* tile_s = cur;
-        __syncthreads();
         if (active) {
             const R* tile = tile_s;
             R pm, pp, pbar[NDIM], diss = R(0);
