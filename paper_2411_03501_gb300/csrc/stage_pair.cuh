@@ -105,8 +105,18 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
         kinds |= kind << (2 * k);
         e_off[k] = (kind == 0u) ? ja * sA + jb : (kind == 1u ? ja : (kind == 2u ? jb : 0));
     }
+    // tiles whose halo lies inside the grid in A and B load without ghost
+    // handling (block-uniform); nvalid = slots inside the tile
+    const bool inner = a0 - G >= 0 && a0 + TA + G <= nA && b0 - G >= 0 && b0 + TB + G <= nB;
+    const int nvalid = min(MAXE, max(0, (HW - tid + nthr - 1) / nthr));
     auto fetch = [&](int s, float* pf) {
         const float* plane = a.phi_s + base_outer + s * sS;
+        if (inner) {
+#pragma unroll
+            for (int k = 0; k < MAXE; ++k)
+                if (k < nvalid) pf[k] = __ldg(plane + e_off[k]);
+            return;
+        }
 #pragma unroll
         for (int k = 0; k < MAXE; ++k) {
             const unsigned kind = (kinds >> (2 * k)) & 3u;
@@ -127,8 +137,14 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
     float pfA[MAXE], pfB[MAXE];
     fetch(s_begin, pfA);
     fetch(min(s_begin + 1, nS - 1), pfB);
-    float wnA = line_value(col, s_begin + G, nS, sS, a.periodic[AS]);
-    float wnB = line_value(col, s_begin + G + 1, nS, sS, a.periodic[AS]);
+    // value j >= 0 of this thread's column along S (plain load inside the grid)
+    auto col_value = [&](int j) -> float {
+        if (j < nS) return __ldg(col + j * sS);
+        return line_value(col, j, nS, sS, a.periodic[AS]);
+    };
+    float wnA = col_value(s_begin + G);
+    float wnB = col_value(s_begin + G + 1);
+    bool nonfinite = false;
     // FACES: left-biased correction of node s from the face s - 1/2 (values
     // s-3 .. s+2 = w[0..5] at the start of the chunk)
     float phim_next = 0.f;
@@ -155,8 +171,8 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
         if (s + 2 < s_end) {
             fetch(s + 2, pfA);
             fetch(min(s + 3, nS - 1), pfB);
-            wnA = line_value(col, s + 2 + G, nS, sS, a.periodic[AS]);
-            wnB = line_value(col, s + 3 + G, nS, sS, a.periodic[AS]);
+            wnA = col_value(s + 2 + G);
+            wnB = col_value(s + 3 + G);
         }
         if (active) {
             const bool second = s + 1 < s_end;
@@ -193,12 +209,19 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
             diss = fma2(F2(0.5f * alpha[AB]), pp - pm, diss);
             if constexpr (NDIM == 4) {
                 const float* c0 = a.phi_s + s * sS + ia * sA + ib;
-                const int s2 = second ? s + 1 : s;
+                const float* c1 = c0 + (second ? sS : 0);
+                if (outer >= G && outer + G < a.n[0]) {  // block-uniform: no ghost cells
 #pragma unroll
-                for (int o = -G; o <= G; ++o)
-                    u[o + G] = F2(line_value(c0, outer + o, a.n[0], a.stride[0], a.periodic[0]),
-                                  line_value(c0 + (s2 - s) * sS, outer + o, a.n[0], a.stride[0],
-                                             a.periodic[0]));
+                    for (int o = -G; o <= G; ++o)
+                        u[o + G] = F2(__ldg(c0 + (outer + o) * a.stride[0]),
+                                      __ldg(c1 + (outer + o) * a.stride[0]));
+                } else {
+#pragma unroll
+                    for (int o = -G; o <= G; ++o)
+                        u[o + G] = F2(line_value(c0, outer + o, a.n[0], a.stride[0], a.periodic[0]),
+                                      line_value(c1, outer + o, a.n[0], a.stride[0],
+                                                 a.periodic[0]));
+                }
                 deriv_weno5_jp2(u, a.inv_dx[0], weno_floor12(a.inv_dx[0]), pm, pp);
                 pbar[0] = F2(0.5f) * (pp + pm);
                 diss = fma2(F2(0.5f * alpha[0]), pp - pm, diss);
@@ -210,14 +233,14 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
             F2 v = fma2(cs, center, cl * L);
             if (a.phi_n) v = fma2(cn, F2(a.phi_n[idx], second ? a.phi_n[idx + sS] : 0.f), v);
             if (a.tube) v = min2(v, F2(__ldg(a.target + idx), second ? __ldg(a.target + idx + sS) : 0.f));
-            if (!isfinite(v.x()) || (second && !isfinite(v.y())))
-                atomicOr(&a.ctl->flags, kFlagNonFinite);
+            nonfinite |= !isfinite(v.x()) || (second && !isfinite(v.y()));
             a.out[idx] = v.x();
             if (second) a.out[idx + sS] = v.y();
         }
 #pragma unroll
         for (int o = 0; o < 2 * G; ++o) w[o] = w[o + 2];
     }
+    if (nonfinite) atomicOr(&a.ctl->flags, kFlagNonFinite);
 }
 
 // Single-problem launch of the paired body (WENO5, FP32): blockDim = (tb,

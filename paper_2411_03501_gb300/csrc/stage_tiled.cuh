@@ -200,9 +200,19 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
         kinds |= kind << (2 * k);
         e_off[k] = (kind == 0u) ? ja * sA + jb : (kind == 1u ? ja : (kind == 2u ? jb : 0));
     }
+    // Tiles whose halo lies inside the grid in A and B (block-uniform) load
+    // their slots without ghost handling; nvalid = slots inside the tile.
+    const bool inner = a0 - G >= 0 && a0 + TA + G <= nA && b0 - G >= 0 && b0 + TB + G <= nB;
+    const int nvalid = min(MAXE, max(0, (H * W - tid + nthr - 1) / nthr));
     // Fetch this thread's slots of plane s (ghost values substituted).
     auto fetch = [&](int s, R* pf) {
         const R* plane = a.phi_s + base_outer + s * sS;
+        if (inner) {
+#pragma unroll
+            for (int k = 0; k < MAXE; ++k)
+                if (k < nvalid) pf[k] = ld_in<COH>(plane + e_off[k]);
+            return;
+        }
 #pragma unroll
         for (int k = 0; k < MAXE; ++k) {
             const unsigned kind = (kinds >> (2 * k)) & 3u;
@@ -222,8 +232,14 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
     };
     R pf[MAXE];
     fetch(s_begin, pf);
+    // value j of this thread's column along S (plain load inside the grid)
+    auto col_value = [&](int j) -> R {
+        if (j < nS) return ld_in<COH>(col + j * sS);
+        return line_value<R, COH>(col, j, nS, sS, a.periodic[AS]);
+    };
     R wnext = R(0);
-    if constexpr (HAS_S) wnext = line_value<R, COH>(col, s_begin + G, nS, sS, a.periodic[AS]);
+    if constexpr (HAS_S) wnext = col_value(s_begin + G);
+    bool nonfinite = false;
 
     for (int s = s_begin; s < s_end; ++s) {
         // double buffer: the buffer written here was last read two planes
@@ -236,7 +252,7 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
         __syncthreads();  // plane s staged
         if (s + 1 < s_end) {  // issue plane s+1's loads before computing plane s
             fetch(s + 1, pf);
-            if constexpr (HAS_S) wnext = line_value<R, COH>(col, s + 1 + G, nS, sS, a.periodic[AS]);
+            if constexpr (HAS_S) wnext = col_value(s + 1 + G);
         }
         const R* tile_s = cur;
         if (active) {
@@ -269,9 +285,16 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
                 // axis 0 (a grid dimension): window straight from global memory
                 R u[2 * G + 1];
                 const R* col0 = a.phi_s + s * sS + ia * sA + ib;
+                if (outer >= G && outer + G < a.n[0]) {  // block-uniform: no ghost cells
 #pragma unroll
-                for (int o = -G; o <= G; ++o)
-                    u[o + G] = line_value<R, COH>(col0, outer + o, a.n[0], a.stride[0], a.periodic[0]);
+                    for (int o = -G; o <= G; ++o)
+                        u[o + G] = ld_in<COH>(col0 + (outer + o) * a.stride[0]);
+                } else {
+#pragma unroll
+                    for (int o = -G; o <= G; ++o)
+                        u[o + G] = line_value<R, COH>(col0, outer + o, a.n[0], a.stride[0],
+                                                      a.periodic[0]);
+                }
                 deriv_fast<SCHEME>(u, a.inv_dx[0], weno_floor12(a.inv_dx[0]), pm, pp);
                 pbar[0] = R(0.5) * (pp + pm);
                 diss += alpha[0] * R(0.5) * (pp - pm);
@@ -283,7 +306,7 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
             R v = a.c_s * center + cl * L;
             if (a.phi_n) v += a.c_n * (COH ? __ldcg(a.phi_n + idx) : a.phi_n[idx]);
             if (a.tube) v = rmin(v, __ldg(a.target + idx));
-            if (!isfinite(v)) atomicOr(&a.ctl->flags, kFlagNonFinite);
+            nonfinite |= !isfinite(v);
             a.out[idx] = v;
         }
         if constexpr (HAS_S) {
@@ -291,6 +314,7 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
             for (int o = 0; o < 2 * G; ++o) w[o] = w[o + 1];
         }
     }
+    if (nonfinite) atomicOr(&a.ctl->flags, kFlagNonFinite);
 }
 
 // Single-problem launch: blockDim = (tb, ta); gridDim = (ceil(nB/tb),
