@@ -12,7 +12,9 @@ Problem description (a plain dict, produced by the seeded input generators):
     {"ndim": d, "n": [...], "lo": [...], "hi": [...], "periodic": [...],
      "scheme": "upwind1" | "eno2" | "eno3" | "weno5",
      "dyn": "normal_speed" | "translate" | "quadratic" | "air3d" | "car4d",
-     "params": [...]}
+     "params": [...],
+     "diss": "glf" | "llf" | "lllf"   (optional, default "glf"),
+     "varform": bool                   (optional: the variational BRT form)}
 
 Function-level citations are in the C source; each wrapper below names the
 passage of the paper its C function follows.
@@ -34,17 +36,22 @@ SCHEMES = {"upwind1": 0, "eno2": 1, "eno3": 2, "weno5": 3}
 DYNAMICS = {"normal_speed": 0, "translate": 1, "quadratic": 2, "air3d": 3, "car4d": 4}
 
 
+DISSIPATION = {"glf": 0, "llf": 1, "lllf": 2}
+
+
 class _Problem(ctypes.Structure):
     _fields_ = [
         ("ndim", ctypes.c_int),
         ("scheme", ctypes.c_int),
         ("dyn", ctypes.c_int),
-        ("pad_", ctypes.c_int),
+        ("diss", ctypes.c_int),
         ("n", ctypes.c_int64 * 4),
         ("lo", ctypes.c_double * 4),
         ("hi", ctypes.c_double * 4),
         ("periodic", ctypes.c_int * 4),
         ("prm", ctypes.c_double * 8),
+        ("varform", ctypes.c_int),
+        ("pad_", ctypes.c_int),
     ]
 
 
@@ -132,6 +139,8 @@ def _problem(spec: dict) -> _Problem:
     p.ndim = d
     p.scheme = SCHEMES[spec["scheme"]]
     p.dyn = DYNAMICS[spec["dyn"]]
+    p.diss = DISSIPATION[spec.get("diss", "glf")]
+    p.varform = 1 if spec.get("varform", False) else 0
     for k in range(d):
         p.n[k] = int(spec["n"][k])
         p.lo[k] = float(spec["lo"][k])

@@ -50,16 +50,22 @@ enum {
     ORC_DYN_CAR4D = 4         /* car (x, y, theta, v), reach game            */
 };
 
+/* dissipation coefficient variants (artificialDissipationGLF of Listing 4
+ * and its local siblings of the toolbox the paper follows) */
+enum { ORC_DISS_GLF = 0, ORC_DISS_LLF = 1, ORC_DISS_LLLF = 2 };
+
 typedef struct {
     int ndim;
     int scheme;
     int dyn;
-    int pad_;
+    int diss;    /* ORC_DISS_*                                              */
     int64_t n[ORC_MAXD];
     double lo[ORC_MAXD];
     double hi[ORC_MAXD];
     int periodic[ORC_MAXD];
     double prm[8];
+    int varform; /* 1: the variational form of the BRT PDE (rate <= 0)    */
+    int pad_;
 } orc_problem;
 
 typedef struct {
@@ -425,7 +431,7 @@ static double partial_bound(const orc_problem* P, const double* x, int k)
 {
     const double* c = P->prm;
     switch (P->dyn) {
-    case ORC_DYN_NORMAL_SPEED: return c[0];
+    case ORC_DYN_NORMAL_SPEED: return fabs(c[0]); /* |dH/dp_k| = |a| |p_k| / |p| */
     case ORC_DYN_TRANSLATE: return fabs(c[k]);
     case ORC_DYN_AIR3D: {
         double ve = c[0], vp = c[1], we = c[2], wp = c[3];
@@ -441,6 +447,17 @@ static double partial_bound(const orc_problem* P, const double* x, int k)
     }
     }
     return 0.0;
+}
+
+/* Bound on |dH/dp_k| at state x over the costate box [clo_j, chi_j] of
+ * every dimension j (the "partialFunc" of Listing 4 receives the costate
+ * range).  The state-only bounds ignore the box; for H = |p|^2/2,
+ * dH/dp_k = p_k and the bound over the box is max(|clo_k|, |chi_k|).       */
+static double partial_bound_box(const orc_problem* P, const double* x, const double* clo,
+                                const double* chi, int k)
+{
+    if (P->dyn == ORC_DYN_QUADRATIC) return fmax(fabs(clo[k]), fabs(chi[k]));
+    return partial_bound(P, x, k);
 }
 
 static void node_coords(const orc_problem* P, int64_t idx, double* x)
@@ -491,8 +508,22 @@ static void alpha_from(const orc_problem* P, double* const* pm, double* const* p
  * conservation-law scheme):
  *   Hhat(x) = H(x, (p^+ + p^-)/2) - sum_k alpha_k (p^+_k - p^-_k)/2
  * and the method-of-lines rate (Sec. V-A, Eq. 24) is L = -Hhat.
+ * Dissipation coefficients (P->diss):
+ *   GLF   alpha_k: one number per dimension, the grid maximum of the bound
+ *         over the global costate box (alpha_from; alpha_in overrides it)
+ *   LLF   alpha_k(x): the bound at node x over the box that is the node's
+ *         own [min, max] of p^-_k, p^+_k in dimension k and the global
+ *         costate range in the other dimensions
+ *   LLLF  alpha_k(x): the bound at node x over the node's own box in every
+ *         dimension
+ * (the paper names only the global routine; the local ones are its
+ * siblings in the toolbox whose layout the paper follows).
+ * Variational form (P->varform, Eq. 30): in time-to-go, with this sign
+ * convention, phi_t + min[0, H] = 0 of the paper's backward-time statement
+ * becomes phi_t = min(0, L): every stage's rate is clipped at zero, so
+ * phi never increases.
  * If alpha_in is NULL alpha is computed from this phi (alpha_out, nullable,
- * receives it).  rate: N doubles.                                          */
+ * receives the GLF coefficients in every mode).  rate: N doubles.          */
 int orc_rate(const orc_problem* P, const double* phi, const double* alpha_in,
              double* alpha_out, double* rate)
 {
@@ -515,17 +546,38 @@ int orc_rate(const orc_problem* P, const double* phi, const double* alpha_in,
         }
         if (alpha_out)
             for (int k = 0; k < d; ++k) alpha_out[k] = alpha[k];
+        /* global costate box, for the local variants */
+        double glo[ORC_MAXD], ghi[ORC_MAXD];
+        for (int k = 0; k < d; ++k) {
+            glo[k] = INFINITY;
+            ghi[k] = -INFINITY;
+            for (int64_t i = 0; i < N; ++i) {
+                glo[k] = fmin(glo[k], fmin(pm[k][i], pp[k][i]));
+                ghi[k] = fmax(ghi[k], fmax(pm[k][i], pp[k][i]));
+            }
+        }
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < N; ++i) {
             double x[ORC_MAXD], pbar[ORC_MAXD];
             node_coords(P, i, x);
             double diss = 0.0;
             for (int k = 0; k < d; ++k) {
+                double ak = alpha[k];
+                if (P->diss != ORC_DISS_GLF) {
+                    double clo[ORC_MAXD], chi[ORC_MAXD];
+                    for (int j = 0; j < d; ++j) {
+                        int local = (P->diss == ORC_DISS_LLLF) || (j == k);
+                        clo[j] = local ? fmin(pm[j][i], pp[j][i]) : glo[j];
+                        chi[j] = local ? fmax(pm[j][i], pp[j][i]) : ghi[j];
+                    }
+                    ak = partial_bound_box(P, x, clo, chi, k);
+                }
                 pbar[k] = 0.5 * (pp[k][i] + pm[k][i]);
-                diss += alpha[k] * 0.5 * (pp[k][i] - pm[k][i]);
+                diss += ak * 0.5 * (pp[k][i] - pm[k][i]);
             }
             double hhat = ham(P, x, pbar) - diss;
             rate[i] = -hhat;
+            if (P->varform && rate[i] > 0.0) rate[i] = 0.0;
         }
     }
     for (int k = 0; k < d; ++k) {
@@ -561,7 +613,9 @@ int orc_alpha(const orc_problem* P, const double* phi, double* alpha)
 }
 
 /* CFL step (Sec. IV-D: lambda max|f'| <= 1; Sec. V-A: adaptive step):
- *   dt = min(cfl / sum_k(alpha_k / dx_k), t_final - t).                     */
+ *   dt = min(cfl / sum_k(alpha_k / dx_k), t_final - t)
+ * with the GLF coefficients in every dissipation mode: the local
+ * coefficients' grid maxima are the GLF ones for every bound above.        */
 double orc_cfl_dt(const orc_problem* P, const double* alpha, double cfl, double t,
                   double t_final)
 {
@@ -889,7 +943,7 @@ static void alpha_grads(const orc_problem* P, double* dalpha /* [4][8] */)
         node_coords(P, at[k], x);
         double* g = dalpha + 8 * k;
         switch (P->dyn) {
-        case ORC_DYN_NORMAL_SPEED: g[0] = 1.0; break;
+        case ORC_DYN_NORMAL_SPEED: g[0] = sgn1(c[0]); break; /* d|a|/da */
         case ORC_DYN_TRANSLATE: g[k] = sgn1(c[k]); break;
         case ORC_DYN_AIR3D:
             if (k == 0) {
@@ -1039,6 +1093,7 @@ int orc_adjoint(const orc_problem* P, const double* phi0, const double* g, int r
                 double* phiT)
 {
     if (P->dyn == ORC_DYN_QUADRATIC) return -5;
+    if (P->diss != ORC_DISS_GLF || P->varform) return -6; /* reverse of the GLF form only */
     int d = P->ndim;
     int64_t N = orc_npoints(P);
     double alpha[ORC_MAXD];

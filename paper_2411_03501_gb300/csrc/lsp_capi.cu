@@ -1167,7 +1167,7 @@ void alpha_param_grads(const lsp_grid* g, const double* x, int k, double* gk)
     for (int j = 0; j < LSP_NPARAM; ++j) gk[j] = 0.0;
     auto sg = [](double v) { return v >= 0.0 ? 1.0 : -1.0; };
     switch (g->dyn) {
-    case LSP_DYN_NORMAL_SPEED: gk[0] = 1.0; break;
+    case LSP_DYN_NORMAL_SPEED: gk[0] = g->prm[0] >= 0.0 ? 1.0 : -1.0; break;  // d|a|/da
     case LSP_DYN_TRANSLATE: gk[k] = sg(c[k]); break;
     case LSP_DYN_AIR3D:
         if (k == 0) {

@@ -215,7 +215,7 @@ template <int DYN>
 __device__ __forceinline__ double partial_bound(const double* x, int k, const double* prm)
 {
     if constexpr (DYN == NORMAL_SPEED) {
-        return prm[0];
+        return fabs(prm[0]);  // |dH/dp_k| = |a| |p_k| / |p| <= |a|
     } else if constexpr (DYN == TRANSLATE) {
         return fabs(prm[k]);
     } else if constexpr (DYN == AIR3D) {

@@ -33,9 +33,13 @@ TWO_PI = 2.0 * math.pi
 
 
 def problem(ndim, n, lo, hi, periodic, scheme, dyn, params, *, rk=3, cfl=0.75,
-            t_final=1.0, dtype="f32", tube=False, name=""):
-    """A problem description as a plain dict (no behaviour attached)."""
+            t_final=1.0, dtype="f32", tube=False, name="", diss="glf", varform=False):
+    """A problem description as a plain dict (no behaviour attached).
+    diss: "glf" | "llf" | "lllf" dissipation coefficients; varform: the
+    variational form of the reachable-tube PDE (rate clipped at zero)."""
     return {
+        "diss": diss,
+        "varform": bool(varform),
         "name": name,
         "ndim": int(ndim),
         "n": [int(v) for v in n],

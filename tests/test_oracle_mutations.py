@@ -1,7 +1,8 @@
 """The oracle's pins are discriminating: each plausible mistake planted in a
 copy of the oracle source (a flipped sign, a wrong index or coefficient, a
 swapped operand) makes at least one pin fail -- test_oracle_pins.py for the
-forward scheme, test_oracle_adjoint.py for the discrete adjoint.  The first
+forward scheme, test_oracle_adjoint.py for the discrete adjoint,
+test_oracle_variants.py for the local dissipation and the variational form.  The first
 occurrence of each anchor is mutated (the forward code precedes the adjoint
 code that mirrors some of its lines).
 
@@ -45,8 +46,8 @@ MUTANTS = {
                            "ext[G - k] = line[0] - (double)k * (line[0] - line[1]);"),
     "periodic_wrap_off_by_one": ("ext[G + n - 1 + k] = line[(k - 1) % n];",
                                  "ext[G + n - 1 + k] = line[k % n];"),
-    "dissipation_sign": ("diss += alpha[k] * 0.5 * (pp[k][i] - pm[k][i]);",
-                         "diss -= alpha[k] * 0.5 * (pp[k][i] - pm[k][i]);"),
+    "dissipation_sign": ("diss += ak * 0.5 * (pp[k][i] - pm[k][i]);",
+                         "diss -= ak * 0.5 * (pp[k][i] - pm[k][i]);"),
     "rk2_average": ("phi[i] = 0.5 * (phi[i] + p1[i] + dt * L[i]);",
                     "phi[i] = 0.5 * (phi[i] + p1[i]) + dt * L[i];"),
     "rk3_second_stage": ("p2[i] = 0.75 * phi[i] + 0.25 * (p1[i] + dt * L[i]);",
@@ -80,13 +81,30 @@ ADJOINT_MUTANTS = {
 }
 
 
+# mistakes in the local dissipation coefficients and the variational form,
+# caught by test_oracle_variants.py
+VARIANT_MUTANTS = {
+    "varform_clip_wrong_side": ("if (P->varform && rate[i] > 0.0) rate[i] = 0.0;",
+                                "if (P->varform && rate[i] < 0.0) rate[i] = 0.0;"),
+    "llf_own_dimension_global": ("int local = (P->diss == ORC_DISS_LLLF) || (j == k);",
+                                 "int local = (P->diss == ORC_DISS_LLLF) || (j != k);"),
+    "box_bound_without_abs": ("if (P->dyn == ORC_DYN_QUADRATIC) return fmax(fabs(clo[k]), fabs(chi[k]));",
+                              "if (P->dyn == ORC_DYN_QUADRATIC) return fmax(clo[k], chi[k]);"),
+    "normal_speed_bound_signed": ("case ORC_DYN_NORMAL_SPEED: return fabs(c[0]);",
+                                  "case ORC_DYN_NORMAL_SPEED: return c[0];"),
+}
+PIN_FILE = {**{k: "test_oracle_pins.py" for k in MUTANTS},
+            **{k: "test_oracle_adjoint.py" for k in ADJOINT_MUTANTS},
+            **{k: "test_oracle_variants.py" for k in VARIANT_MUTANTS}}
+
+
 @pytest.mark.slow
 @pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
-@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(ADJOINT_MUTANTS))
+@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(ADJOINT_MUTANTS) +
+                         sorted(VARIANT_MUTANTS))
 def test_planted_mistake_is_caught(tmp_path, name):
     src = open(SRC).read()
-    adjoint = name in ADJOINT_MUTANTS
-    old, new = (ADJOINT_MUTANTS if adjoint else MUTANTS)[name]
+    old, new = {**MUTANTS, **ADJOINT_MUTANTS, **VARIANT_MUTANTS}[name]
     old, new = old.replace("\\n", "\n"), new.replace("\\n", "\n")
     assert src.count(old) >= 1, f"mutation anchor for {name} not found"
     c = tmp_path / "mutant.c"
@@ -95,8 +113,7 @@ def test_planted_mistake_is_caught(tmp_path, name):
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", str(c), "-o", str(so), "-lm"],
                    check=True)
     r = subprocess.run(
-        [sys.executable, "-m", "pytest",
-         os.path.join(HERE, "test_oracle_adjoint.py" if adjoint else "test_oracle_pins.py"), "-x",
+        [sys.executable, "-m", "pytest", os.path.join(HERE, PIN_FILE[name]), "-x",
          "-q", "-p", "no:cacheprovider"],
         env=dict(os.environ, LSP_ORACLE_LIB=str(so)), capture_output=True, text=True,
         timeout=600)
