@@ -68,16 +68,36 @@ typedef enum { LSP_UPWIND1 = 0, LSP_ENO2 = 1, LSP_ENO3 = 2, LSP_WENO5 = 3 } lsp_
  *                        minimises; H = -max_u min_d p.f      {v_e, v_p, u_max, d_max}
  *  CAR4D         d = 4   car (x, y, theta, v), turn rate and
  *                        acceleration minimise p.f (reach)     {w_max, a_max}
+ *  ROCKETS       d = 3   two rockets (Sec. VI-A, Eq. 31), relative
+ *                        (x, z, theta): f = (a cos th + u_e x,
+ *                        a sin th + a + u_p x - g, u_p - u_e); evader
+ *                        thrust angle u_e in [-ue, ue] maximises,
+ *                        pursuer u_p in [-up, up] minimises    {a, g, ue, up}
+ *  DOUBLE_INTEGRATOR d = 2  x1dot = x2, x2dot = u, |u| <= umax,
+ *                        u minimises p.f (reach)                {umax}
+ * The adjoint covers NORMAL_SPEED, TRANSLATE, AIR3D and CAR4D.
  */
 typedef enum {
     LSP_DYN_NORMAL_SPEED = 0,
     LSP_DYN_TRANSLATE = 1,
     LSP_DYN_QUADRATIC = 2,
     LSP_DYN_AIR3D = 3,
-    LSP_DYN_CAR4D = 4
+    LSP_DYN_CAR4D = 4,
+    LSP_DYN_ROCKETS = 5,
+    LSP_DYN_DOUBLE_INTEGRATOR = 6
 } lsp_dyn;
 
 typedef enum { LSP_F32 = 0, LSP_F64 = 1 } lsp_dtype;
+
+/* Dissipation coefficients of the Lax-Friedrichs term (Sec. IV-D).  GLF:
+ * alpha_k is the grid maximum of the bound on |dH/dp_k| (the routine the
+ * paper's Listing 4 names).  LLF / LLLF: the bound at each node, over the
+ * node's own costate interval in dimension k (LLF) or in every dimension
+ * (LLLF) and the global interval elsewhere.  The bounds of the dynamics
+ * provided involve at most the costate of their own dimension, so LLF and
+ * LLLF coincide for them.  The CFL step uses the grid maxima, which are the
+ * GLF coefficients in every mode. */
+typedef enum { LSP_DISS_GLF = 0, LSP_DISS_LLF = 1, LSP_DISS_LLLF = 2 } lsp_diss;
 
 typedef struct lsp_grid lsp_grid; /* opaque: grid + dynamics */
 
@@ -105,7 +125,13 @@ typedef struct {
     int batch_wait_ms; /* persistent batched solves: limit of one device
                           wait in milliseconds (0 = 1000); a wait that runs
                           out ends the launch with LSP_ETIMEOUT            */
-    int reserved[3];   /* must be zero                                     */
+    int diss;          /* lsp_diss (0 = GLF)                               */
+    int varform;       /* 1: the variational form of the reachable-tube PDE
+                          (Eq. 30: phi_t + min[0, H] = 0 in the paper's
+                          backward time; here every stage rate L = -Hhat is
+                          replaced by min(L, 0), so phi never increases).
+                          Independent of tube.                             */
+    int reserved[1];   /* must be zero                                     */
 } lsp_solve_opts;
 
 typedef struct {
@@ -327,6 +353,51 @@ lsp_status lsp_hj_adjoint(lsp_grid* grid, const lsp_solve_opts* opts, const void
  * Asynchronous. */
 lsp_status lsp_loss_tube(const lsp_grid* grid, int dtype, const void* phi, const void* queries,
                          int nq, double* value_dev, void* grad, void* stream);
+
+/* Implicit surfaces (Sec. III-C, III-D): fields built on the device, for
+ * targets and initial conditions.  Each primitive writes, at every node of
+ * `grid` (coordinates lo + i dx, C order), a value whose zero level set is
+ * the shape and which is negative inside; distances are measured in the
+ * dimensions whose bit is clear in `ignore_mask` (bit k = dimension k), so
+ * ignoring dimensions extrudes the shape along them (a sphere becomes a
+ * cylinder).  Periodic axes are not wrapped.  Arithmetic in FP64, stored
+ * in `dtype`; `out` is a device field of the grid's size.  Asynchronous.
+ *  lsp_shape_sphere     |x - center| - radius (signed distance)
+ *  lsp_shape_box        signed distance to the box [lo, hi] (exact: the
+ *                       Euclidean distance outside, minus the distance to
+ *                       the nearest face inside)
+ *  lsp_shape_quadric    sum_k w_k (x_k - center_k)^2 - offset: the
+ *                       ellipsoid form of Sec. III-C (not a distance)
+ *  lsp_shape_halfspace  n . (x - point) / |n| (signed distance to the plane;
+ *                       polyhedra are intersections of half spaces)
+ * LSP_EINVAL for a NULL pointer, an unset grid, all dimensions ignored, a
+ * negative radius, lo > hi or a zero normal. */
+lsp_status lsp_shape_sphere(const lsp_grid* grid, int dtype, const double* center, double radius,
+                            unsigned ignore_mask, void* out, void* stream);
+lsp_status lsp_shape_box(const lsp_grid* grid, int dtype, const double* lo, const double* hi,
+                         unsigned ignore_mask, void* out, void* stream);
+lsp_status lsp_shape_quadric(const lsp_grid* grid, int dtype, const double* center,
+                             const double* weights, double offset, unsigned ignore_mask,
+                             void* out, void* stream);
+lsp_status lsp_shape_halfspace(const lsp_grid* grid, int dtype, const double* normal,
+                               const double* point, unsigned ignore_mask, void* out,
+                               void* stream);
+
+/* Calculus on implicit functions (Sec. III-D), elementwise over n values of
+ * `dtype` (device arrays; out may alias a or b):
+ *  UNION       min(a, b)       interior of either
+ *  INTERSECT   max(a, b)       interior of both
+ *  COMPLEMENT  -a              (b unused, may be NULL)
+ *  DIFFERENCE  max(a, -b)      interior of a outside b
+ * Asynchronous. */
+typedef enum {
+    LSP_SHAPE_UNION = 0,
+    LSP_SHAPE_INTERSECT = 1,
+    LSP_SHAPE_COMPLEMENT = 2,
+    LSP_SHAPE_DIFFERENCE = 3
+} lsp_shape_op_kind;
+lsp_status lsp_shape_op(int op, int dtype, const void* a, const void* b, void* out, int64_t n,
+                        void* stream);
 
 /* Wait for `stream` and report a device-side failure flagged in the
  * workspace control block since the last call that reset it (every step

@@ -11,7 +11,8 @@ Problem description (a plain dict, produced by the seeded input generators):
 
     {"ndim": d, "n": [...], "lo": [...], "hi": [...], "periodic": [...],
      "scheme": "upwind1" | "eno2" | "eno3" | "weno5",
-     "dyn": "normal_speed" | "translate" | "quadratic" | "air3d" | "car4d",
+     "dyn": "normal_speed" | "translate" | "quadratic" | "air3d" | "car4d" |
+            "rockets" | "double_integrator",
      "params": [...],
      "diss": "glf" | "llf" | "lllf"   (optional, default "glf"),
      "varform": bool                   (optional: the variational BRT form)}
@@ -33,7 +34,8 @@ _SRC = os.path.join(_HERE, "lsp_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_lib", "liblsp_oracle.so")
 
 SCHEMES = {"upwind1": 0, "eno2": 1, "eno3": 2, "weno5": 3}
-DYNAMICS = {"normal_speed": 0, "translate": 1, "quadratic": 2, "air3d": 3, "car4d": 4}
+DYNAMICS = {"normal_speed": 0, "translate": 1, "quadratic": 2, "air3d": 3, "car4d": 4,
+            "rockets": 5, "double_integrator": 6}
 
 
 DISSIPATION = {"glf": 0, "llf": 1, "lllf": 2}

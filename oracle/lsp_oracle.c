@@ -47,7 +47,9 @@ enum {
     ORC_DYN_TRANSLATE = 1,    /* H = v . p                                   */
     ORC_DYN_QUADRATIC = 2,    /* H = |p|^2 / 2   (alpha depends on p)        */
     ORC_DYN_AIR3D = 3,        /* relative pursuit-evasion (x, y, theta)      */
-    ORC_DYN_CAR4D = 4         /* car (x, y, theta, v), reach game            */
+    ORC_DYN_CAR4D = 4,        /* car (x, y, theta, v), reach game            */
+    ORC_DYN_ROCKETS = 5,      /* two rockets, relative (x, z, theta), game   */
+    ORC_DYN_DOUBLE_INT = 6    /* double integrator (x1, x2), reach           */
 };
 
 /* dissipation coefficient variants (artificialDissipationGLF of Listing 4
@@ -225,21 +227,31 @@ static double eno_eval(const double* u, int64_t i, int64_t k, double dx, int ord
 }
 
 /* The ENO derivative, and in *flip (nullable) the largest change of it that
- * taking a near-tied selection (rel_gap < 1e-4) the other way would cause;
- * 0 when no selection is near a tie.  (*flip is diagnostic output for the
- * comparisons with other implementations; it enters no computed value.) */
+ * taking a near-tied selection the other way would cause; 0 when no
+ * selection is near a tie.  Near a tie: the compared magnitudes differ by
+ * less than 1e-4 of their sum, or by less than what FP32 rounding of the
+ * window values can move a divided difference (about 4 ulps of the largest
+ * |u| in the window for a second difference, 8 for a third, over their
+ * denominators 2 dx^2 and 6 dx^3, doubled).  (*flip is diagnostic output for
+ * the comparisons with other implementations; it enters no computed value.) */
 static double eno_at(const double* u, int64_t i, int64_t k, double dx, int order, double* flip)
 {
     double r = eno_eval(u, i, k, dx, order, -1, -1);
     if (flip) {
+        const double u32 = 5.9604644775390625e-8; /* 2^-24 */
+        double M = 0.0;
+        for (int o = -order; o <= order; ++o) M = fmax(M, fabs(u[i + o]));
         double fl = 0.0;
         double a = D2(u, k, dx), b = D2(u, k + 1, dx);
         int first = fabs(a) <= fabs(b);
-        if (rel_gap(a, b) < 1e-4) fl = fabs(eno_eval(u, i, k, dx, order, first ? 1 : 0, -1) - r);
+        double tie2 = 8.0 * u32 * M / (2.0 * dx * dx);
+        if (rel_gap(a, b) < 1e-4 || fabs(fabs(a) - fabs(b)) <= tie2)
+            fl = fabs(eno_eval(u, i, k, dx, order, first ? 1 : 0, -1) - r);
         if (order >= 3) {
             int64_t kstar = first ? k - 1 : k;
             double e = D3h(u, kstar, dx), f = D3h(u, kstar + 1, dx);
-            if (rel_gap(e, f) < 1e-4) {
+            double tie3 = 16.0 * u32 * M / (6.0 * dx * dx * dx);
+            if (rel_gap(e, f) < 1e-4 || fabs(fabs(e) - fabs(f)) <= tie3) {
                 double alt = eno_eval(u, i, k, dx, order, first ? 0 : 1,
                                       fabs(e) <= fabs(f) ? 1 : 0);
                 if (fabs(alt - r) > fl) fl = fabs(alt - r);
@@ -421,6 +433,28 @@ static double ham(const orc_problem* P, const double* x, const double* p)
         double m = p[0] * v * cos(th) + p[1] * v * sin(th) - wm * fabs(p[2]) - am * fabs(p[3]);
         return -m;
     }
+    case ORC_DYN_ROCKETS: {
+        /* Sec. VI-A, Eq. 31: f = (a cos th + u_e x, a sin th + a + u_p x - g,
+         * u_p - u_e) with a_e = a_p = a; the evader input u_e in [-ue, ue]
+         * maximises, the pursuer input u_p in [-up, up] minimises, and
+         * H = -max_{u_e} min_{u_p} p.f.  Reading: this definition is used and
+         * its closed form derived from it, because the printed closed form
+         * (Eq. 32) disagrees with it in the sign of the p_2 term and in both
+         * switching terms.  p.f = p1 a cos th + p2 (a sin th + a - g)
+         *   + u_e (p1 x - p3) + u_p (p2 x + p3).                              */
+        double a = c[0], g = c[1], ue = c[2], up = c[3];
+        double X = x[0], th = x[2];
+        double v = p[0] * a * cos(th) + p[1] * (a * sin(th) + a - g) + ue * fabs(p[0] * X - p[2]) -
+                   up * fabs(p[1] * X + p[2]);
+        return -v;
+    }
+    case ORC_DYN_DOUBLE_INT: {
+        /* Table I names the double integrator without stating it.  Reading:
+         * x1dot = x2, x2dot = u, |u| <= umax, the input drives the state into
+         * the target (reach): H = -min_u p.f = -(p1 x2 - umax |p2|).         */
+        double um = c[0];
+        return -(p[0] * x[1] - um * fabs(p[1]));
+    }
     }
     return 0.0;
 }
@@ -445,6 +479,14 @@ static double partial_bound(const orc_problem* P, const double* x, int k)
         if (k == 2) return c[0];
         return c[1];
     }
+    case ORC_DYN_ROCKETS: { /* |dH/dp_k| over both input choices */
+        double a = c[0], g = c[1], ue = c[2], up = c[3];
+        if (k == 0) return a * fabs(cos(x[2])) + ue * fabs(x[0]);
+        if (k == 1) return fabs(a * sin(x[2]) + a - g) + up * fabs(x[0]);
+        return ue + up;
+    }
+    case ORC_DYN_DOUBLE_INT:
+        return k == 0 ? fabs(x[1]) : c[0];
     }
     return 0.0;
 }
@@ -1092,7 +1134,8 @@ int orc_adjoint(const orc_problem* P, const double* phi0, const double* g, int r
                 int64_t nsteps, const double* lamT, double* lam0, double* lam_g, double* dprm,
                 double* phiT)
 {
-    if (P->dyn == ORC_DYN_QUADRATIC) return -5;
+    if (P->dyn == ORC_DYN_QUADRATIC || P->dyn == ORC_DYN_ROCKETS || P->dyn == ORC_DYN_DOUBLE_INT)
+        return -5; /* reverse written for the other dynamics */
     if (P->diss != ORC_DISS_GLF || P->varform) return -6; /* reverse of the GLF form only */
     int d = P->ndim;
     int64_t N = orc_npoints(P);

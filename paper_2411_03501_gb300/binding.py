@@ -17,8 +17,10 @@ LIB_PATH = os.path.join(HERE, "_lib", "liblsp.so")
 LSP_OK, LSP_EINVAL, LSP_ENOMEM, LSP_ECUDA, LSP_EUNSUPPORTED, LSP_ENONFINITE, LSP_ETIMEOUT = range(7)
 BC = {"extrapolate": 0, "periodic": 1}
 SCHEMES = {"upwind1": 0, "eno2": 1, "eno3": 2, "weno5": 3}
-DYNAMICS = {"normal_speed": 0, "translate": 1, "quadratic": 2, "air3d": 3, "car4d": 4}
+DYNAMICS = {"normal_speed": 0, "translate": 1, "quadratic": 2, "air3d": 3, "car4d": 4,
+            "rockets": 5, "double_integrator": 6}
 DTYPES = {"f32": 0, "f64": 1}
+DISSIPATION = {"glf": 0, "llf": 1, "lllf": 2}
 
 # Every symbol the header declares (checked by the ABI test).
 EXPORTS = [
@@ -27,8 +29,10 @@ EXPORTS = [
     "lsp_hj_step", "lsp_hj_solve", "lsp_check_status", "lsp_hj_solve_noalloc",
     "lsp_set_tile", "lsp_get_tile", "lsp_autotune", "lsp_batched_workspace_size",
     "lsp_hj_solve_batched", "lsp_adjoint_workspace_size", "lsp_hj_solve_ckpt", "lsp_hj_adjoint",
-    "lsp_loss_tube", "lsp_debug_stall_problem",
+    "lsp_loss_tube", "lsp_debug_stall_problem", "lsp_shape_sphere", "lsp_shape_box",
+    "lsp_shape_quadric", "lsp_shape_halfspace", "lsp_shape_op",
 ]
+SHAPE_OPS = {"union": 0, "intersect": 1, "complement": 2, "difference": 3}
 
 
 class LspError(RuntimeError):
@@ -49,7 +53,9 @@ class lsp_solve_opts(ctypes.Structure):
         ("batch_chunk", ctypes.c_int),
         ("batch_persistent", ctypes.c_int),
         ("batch_wait_ms", ctypes.c_int),
-        ("reserved", ctypes.c_int * 3),
+        ("diss", ctypes.c_int),
+        ("varform", ctypes.c_int),
+        ("reserved", ctypes.c_int * 1),
     ]
 
 
@@ -96,6 +102,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.lsp_hj_solve.argtypes = [vp, op, vp, vp, ctypes.c_double, ctypes.c_double, vp, sz,
                                ctypes.POINTER(lsp_solve_stats), vp]
     L.lsp_check_status.argtypes = [vp, vp]
+    ui = ctypes.c_uint
+    L.lsp_shape_sphere.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ui, vp, vp]
+    L.lsp_shape_box.argtypes = [vp, ctypes.c_int, dp, dp, ui, vp, vp]
+    L.lsp_shape_quadric.argtypes = [vp, ctypes.c_int, dp, dp, ctypes.c_double, ui, vp, vp]
+    L.lsp_shape_halfspace.argtypes = [vp, ctypes.c_int, dp, dp, ui, vp, vp]
+    L.lsp_shape_op.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.c_int64, vp]
     L.lsp_debug_stall_problem.argtypes = [ctypes.c_int]
     L.lsp_debug_stall_problem.restype = ctypes.c_int
     L.lsp_hj_solve_noalloc.argtypes = [vp, op, vp, vp, ctypes.c_double, ctypes.c_double,
@@ -185,8 +197,10 @@ def lsp_get_alpha(grid: Grid, ndim: int):
 
 
 def make_opts(rk_order=3, scheme="weno5", dtype="f32", tube=False, cfl=0.75, check_finite=False,
-              use_graph=False) -> lsp_solve_opts:
+              use_graph=False, diss="glf", varform=False) -> lsp_solve_opts:
     o = lsp_solve_opts()
+    o.diss = DISSIPATION[diss] if isinstance(diss, str) else int(diss)
+    o.varform = 1 if varform else 0
     o.rk_order = int(rk_order)
     o.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     o.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
@@ -328,7 +342,8 @@ class Batch:
             self.grids.append(g)
         s0 = specs[0]
         self.opts = make_opts(s0.get("rk", 3), s0["scheme"], "f32", s0.get("tube", False),
-                              s0.get("cfl", 0.75), check_finite, use_graph)
+                              s0.get("cfl", 0.75), check_finite, use_graph,
+                              s0.get("diss", "glf"), s0.get("varform", False))
         self.opts.batch_chunk = int(chunk)
         self.opts.batch_persistent = 1 if persistent else 0
         self.opts.batch_wait_ms = int(wait_ms)
@@ -343,6 +358,62 @@ class Batch:
 
 def lsp_check_status(workspace, stream=None):
     _check(load().lsp_check_status(_ptr(workspace), _stream(stream)))
+
+
+def _darr(v, d=4):
+    a = (ctypes.c_double * d)()
+    for i, x in enumerate(v):
+        a[i] = float(x)
+    return a
+
+
+def _mask(ignore) -> int:
+    m = 0
+    for k in ignore or ():
+        m |= 1 << int(k)
+    return m
+
+
+def _dtype_of(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return DTYPES["f64"]
+    if t.dtype == torch.float32:
+        return DTYPES["f32"]
+    raise TypeError("shape fields are float32 or float64 tensors")
+
+
+def lsp_shape_sphere(grid: Grid, out, center, radius, ignore=(), stream=None):
+    """Signed distance to a sphere (a cylinder along the ignored dims)."""
+    _check(load().lsp_shape_sphere(grid.handle, _dtype_of(out), _darr(center), float(radius),
+                                   _mask(ignore), _ptr(out), _stream(stream)))
+    return out
+
+
+def lsp_shape_box(grid: Grid, out, lo, hi, ignore=(), stream=None):
+    _check(load().lsp_shape_box(grid.handle, _dtype_of(out), _darr(lo), _darr(hi), _mask(ignore),
+                                _ptr(out), _stream(stream)))
+    return out
+
+
+def lsp_shape_quadric(grid: Grid, out, center, weights, offset, ignore=(), stream=None):
+    _check(load().lsp_shape_quadric(grid.handle, _dtype_of(out), _darr(center), _darr(weights),
+                                    float(offset), _mask(ignore), _ptr(out), _stream(stream)))
+    return out
+
+
+def lsp_shape_halfspace(grid: Grid, out, normal, point, ignore=(), stream=None):
+    _check(load().lsp_shape_halfspace(grid.handle, _dtype_of(out), _darr(normal), _darr(point),
+                                      _mask(ignore), _ptr(out), _stream(stream)))
+    return out
+
+
+def lsp_shape_op(op, a, b, out, stream=None):
+    """union / intersect / complement / difference of implicit fields."""
+    code = SHAPE_OPS[op] if isinstance(op, str) else int(op)
+    _check(load().lsp_shape_op(code, _dtype_of(a), _ptr(a), _ptr(b), _ptr(out), int(a.numel()),
+                               _stream(stream)))
+    return out
 
 
 def lsp_debug_stall_problem(problem: int) -> int:
@@ -365,7 +436,7 @@ class Problem:
         lsp_set_dynamics(self.grid, spec["dyn"], spec["params"])
         self.opts = make_opts(spec.get("rk", 3), spec["scheme"], spec.get("dtype", "f32"),
                               spec.get("tube", False), spec.get("cfl", 0.75), check_finite,
-                              use_graph)
+                              use_graph, spec.get("diss", "glf"), spec.get("varform", False))
         self.torch_dtype = torch.float64 if spec.get("dtype", "f32") == "f64" else torch.float32
         nbytes = lsp_workspace_size(self.grid, self.opts)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)

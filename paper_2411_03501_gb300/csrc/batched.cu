@@ -14,222 +14,27 @@
 #include <cstring>
 #include <vector>
 
-#include "../../include/lsp.h"
-#include "batched.h"
-#include "launch.h"
-#include "stage_tiled.cuh"
+#include "batched.cuh"
 
 namespace lsp {
 
-// Stage fields and TVD-RK coefficients (Sec. V-A) of stage `stage` of a
-// problem's step; the target only in the last stage.
-__device__ __forceinline__ void batch_stage_args(const BatchProblem& P, int step, int stage, int rk,
-                                                 StageArgs<float>& sa)
+cudaError_t launch_batched(int scheme, const BatchProblem* probs, const int* block_prob, int nblocks,
+                           int step, int stage, int rk, bool local, cudaStream_t s)
 {
-    sa = P.a;
-    sa.dt = float((step == P.nsteps - 1) ? P.dt_last : P.dt);
-    sa.dt_from_ctl = 0;
-    sa.alpha_from_ctl = 0;
-    sa.tube = 0;
-    sa.phi_n = nullptr;
-    if (stage == 0) {
-        sa.phi_s = P.phi; sa.out = P.w1;
-        sa.c_n = 0.f; sa.c_s = 1.f; sa.c_l = 1.f;
-    } else if (stage == 1 && rk == 2) {
-        sa.phi_s = P.w1; sa.phi_n = P.phi; sa.out = P.phi;
-        sa.c_n = 0.5f; sa.c_s = 0.5f; sa.c_l = 0.5f;
-        sa.tube = P.a.tube;
-    } else if (stage == 1) {
-        sa.phi_s = P.w1; sa.phi_n = P.phi; sa.out = P.w2;
-        sa.c_n = 0.75f; sa.c_s = 0.25f; sa.c_l = 0.25f;
-    } else {
-        sa.phi_s = P.w2; sa.phi_n = P.phi; sa.out = P.phi;
-        sa.c_n = float(1.0 / 3.0); sa.c_s = float(2.0 / 3.0); sa.c_l = float(2.0 / 3.0);
-        sa.tube = P.a.tube;
-    }
-    sa.target = P.target;
-}
-
-template <int SCHEME, bool COH>
-__device__ __forceinline__ void batch_tile(const BatchProblem& P, const StageArgs<float>& sa,
-                                           int local, float* tile)
-{
-    const int bx = local % P.nbx;
-    const int by = (local / P.nbx) % P.nby;
-    const int z = local / (P.nbx * P.nby);
-    const int chunk = z % P.nchunks, outer = z / P.nchunks;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    switch (P.ndim * 8 + P.dyn) {
-    case 2 * 8 + NORMAL_SPEED:
-        tiled_stage_body<2, SCHEME, NORMAL_SPEED, float, COH>(sa, kBatchTB, kBatchTA, bx, by, 0, 0, 1, tile, tx, ty);
-        break;
-    case 2 * 8 + TRANSLATE:
-        tiled_stage_body<2, SCHEME, TRANSLATE, float, COH>(sa, kBatchTB, kBatchTA, bx, by, 0, 0, 1, tile, tx, ty);
-        break;
-    case 3 * 8 + NORMAL_SPEED:
-        tiled_stage_body<3, SCHEME, NORMAL_SPEED, float, COH>(sa, kBatchTB, kBatchTA, bx, by, chunk, 0, P.ch, tile, tx, ty);
-        break;
-    case 3 * 8 + TRANSLATE:
-        tiled_stage_body<3, SCHEME, TRANSLATE, float, COH>(sa, kBatchTB, kBatchTA, bx, by, chunk, 0, P.ch, tile, tx, ty);
-        break;
-    case 3 * 8 + AIR3D:
-        tiled_stage_body<3, SCHEME, AIR3D, float, COH>(sa, kBatchTB, kBatchTA, bx, by, chunk, 0, P.ch, tile, tx, ty);
-        break;
-    case 4 * 8 + NORMAL_SPEED:
-        tiled_stage_body<4, SCHEME, NORMAL_SPEED, float, COH>(sa, kBatchTB, kBatchTA, bx, by, chunk, outer, P.ch, tile, tx, ty);
-        break;
-    case 4 * 8 + TRANSLATE:
-        tiled_stage_body<4, SCHEME, TRANSLATE, float, COH>(sa, kBatchTB, kBatchTA, bx, by, chunk, outer, P.ch, tile, tx, ty);
-        break;
-    case 4 * 8 + CAR4D:
-        tiled_stage_body<4, SCHEME, CAR4D, float, COH>(sa, kBatchTB, kBatchTA, bx, by, chunk, outer, P.ch, tile, tx, ty);
-        break;
-    default:
-        break;  // rejected on the host
-    }
-}
-
-// One RK stage of every active problem: CTA i runs tile i - block_start of
-// problem block_prob[i].
-template <int SCHEME>
-__global__ void __launch_bounds__(kBatchTB * kBatchTA, 3)
-    stage_batched_kernel(const BatchProblem* __restrict__ probs, const int* __restrict__ block_prob,
-                         int step, int stage, int rk)
-{
-    constexpr int G = ghost_width(SCHEME);
-    __shared__ StageArgs<float> sa;
-    __shared__ float tile[2 * (kBatchTA + 2 * G) * (kBatchTB + 2 * G)];
-    const int p = block_prob[blockIdx.x];
-    const BatchProblem& P = probs[p];
-    const int tid = threadIdx.y * kBatchTB + threadIdx.x;
-    if (tid == 0) batch_stage_args(P, step, stage, rk, sa);
-    __syncthreads();
-    batch_tile<SCHEME, false>(P, sa, blockIdx.x - P.block_start, tile);
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// The whole batched solve in one launch.  Every CTA takes the next work item
-// (k, s, b) from one counter; items go out in (step, stage, tile) order, so
-// every item an item depends on -- all tiles of the previous stage of the
-// same problem -- was handed out earlier to a CTA that is running (the launch
-// is cooperative: all CTAs are resident).  A CTA waits for its dependency on
-// the problem's completion counter; the wait is bounded by wait_ns, after
-// which it raises kFlagTimeout, sets the abort flag (other waiters leave at
-// once) and stops: the launch always ends.
-template <int SCHEME>
-__global__ void __launch_bounds__(kBatchTB * kBatchTA, 3)
-    stage_batched_persistent(const BatchProblem* __restrict__ probs,
-                             const int* __restrict__ block_prob,
-                             const BatchSegment* __restrict__ segs, int nseg, int rk,
-                             unsigned int* done, PersistCtl* pc, Ctl* ctl,
-                             unsigned long long wait_ns)
-{
-    constexpr int G = ghost_width(SCHEME);
-    __shared__ StageArgs<float> sa;
-    __shared__ float tile[2 * (kBatchTA + 2 * G) * (kBatchTB + 2 * G)];
-    __shared__ int s_p, s_local, s_stop;
-    const int tid = threadIdx.y * kBatchTB + threadIdx.x;
-    const long long total = segs[nseg].item_start;
-    for (;;) {
-        if (tid == 0) {
-            int stop = 0;
-            const long long it = (long long)atomicAdd(&pc->next, 1ULL);
-            if (it >= total || *(volatile unsigned*)&pc->abort) {
-                stop = 1;
-            } else {
-                int lo = 0, hi = nseg;  // segs[lo].item_start <= it < segs[hi].item_start
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (segs[mid].item_start <= it) lo = mid;
-                    else hi = mid;
-                }
-                const BatchSegment sg = segs[lo];
-                const long long off = it - sg.item_start;
-                const long long per_step = (long long)rk * sg.blocks;
-                const int k = sg.k_start + (int)(off / per_step);
-                const int r = (int)(off % per_step);
-                const int stage = r / sg.blocks, b = r % sg.blocks;
-                const int p = block_prob[b];
-                const BatchProblem& P = probs[p];
-                const unsigned target = (unsigned)(k * rk + stage) * (unsigned)P.nblocks;
-                const unsigned long long t0 = global_ns();
-                while (*(volatile unsigned*)(done + p) < target) {
-                    if (*(volatile unsigned*)&pc->abort) {
-                        stop = 1;
-                        break;
-                    }
-                    if (global_ns() - t0 > wait_ns) {
-                        atomicOr(&ctl->flags, kFlagTimeout);
-                        atomicExch(&pc->abort, 1u);
-                        stop = 1;
-                        break;
-                    }
-                    __nanosleep(256);
-                }
-                __threadfence();  // acquire: the producers' stores are visible
-                if (!stop) {
-                    batch_stage_args(P, k, stage, rk, sa);
-                    s_p = p;
-                    s_local = b - P.block_start;
-                }
-            }
-            s_stop = stop;
-        }
-        __syncthreads();
-        if (s_stop) break;
-        batch_tile<SCHEME, true>(probs[s_p], sa, s_local, tile);
-        __syncthreads();
-        if (tid == 0) {
-            __threadfence();  // release this tile's stores before counting it done
-            if (s_p != pc->stall_problem) atomicAdd(done + s_p, 1u);
-        }
-    }
+    if (local) return launch_batched_local(scheme, probs, block_prob, nblocks, step, stage, rk, s);
+    return launch_batched_t<false>(scheme, probs, block_prob, nblocks, step, stage, rk, s);
 }
 
 cudaError_t launch_batched_persistent(int scheme, const BatchProblem* probs, const int* block_prob,
                                       const BatchSegment* segs, int nseg, int rk,
                                       unsigned int* done, PersistCtl* pc, Ctl* ctl,
-                                      unsigned long long wait_ns, cudaStream_t s)
+                                      unsigned long long wait_ns, bool local, cudaStream_t s)
 {
-    const void* fn = nullptr;
-    switch (scheme) {
-    case UPWIND1: fn = (const void*)stage_batched_persistent<UPWIND1>; break;
-    case ENO2: fn = (const void*)stage_batched_persistent<ENO2>; break;
-    case ENO3: fn = (const void*)stage_batched_persistent<ENO3>; break;
-    case WENO5: fn = (const void*)stage_batched_persistent<WENO5>; break;
-    default: return cudaErrorInvalidValue;
-    }
-    int dev = 0, nsm = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (!e) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchTB * kBatchTA, 0);
-    if (e) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    dim3 grid(nsm * per_sm), block(kBatchTB, kBatchTA, 1);
-    void* args[] = {(void*)&probs, (void*)&block_prob, (void*)&segs, (void*)&nseg, (void*)&rk,
-                    (void*)&done, (void*)&pc, (void*)&ctl, (void*)&wait_ns};
-    return cudaLaunchCooperativeKernel(fn, grid, block, args, 0, s);
-}
-
-cudaError_t launch_batched(int scheme, const BatchProblem* probs, const int* block_prob, int nblocks,
-                           int step, int stage, int rk, cudaStream_t s)
-{
-    if (nblocks <= 0) return cudaSuccess;
-    dim3 block(kBatchTB, kBatchTA, 1);
-    switch (scheme) {
-    case UPWIND1: stage_batched_kernel<UPWIND1><<<nblocks, block, 0, s>>>(probs, block_prob, step, stage, rk); break;
-    case ENO2: stage_batched_kernel<ENO2><<<nblocks, block, 0, s>>>(probs, block_prob, step, stage, rk); break;
-    case ENO3: stage_batched_kernel<ENO3><<<nblocks, block, 0, s>>>(probs, block_prob, step, stage, rk); break;
-    case WENO5: stage_batched_kernel<WENO5><<<nblocks, block, 0, s>>>(probs, block_prob, step, stage, rk); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    if (local)
+        return launch_batched_persistent_local(scheme, probs, block_prob, segs, nseg, rk, done, pc,
+                                               ctl, wait_ns, s);
+    return launch_batched_persistent_t<false>(scheme, probs, block_prob, segs, nseg, rk, done, pc,
+                                              ctl, wait_ns, s);
 }
 
 void batch_tile_dims(int* tb, int* ta)
@@ -240,8 +45,8 @@ void batch_tile_dims(int* tb, int* ta)
 
 bool batch_supported(int ndim, int dyn)
 {
-    if (ndim == 2) return dyn == NORMAL_SPEED || dyn == TRANSLATE;
-    if (ndim == 3) return dyn == NORMAL_SPEED || dyn == TRANSLATE || dyn == AIR3D;
+    if (ndim == 2) return dyn == NORMAL_SPEED || dyn == TRANSLATE || dyn == DOUBLE_INT;
+    if (ndim == 3) return dyn == NORMAL_SPEED || dyn == TRANSLATE || dyn == AIR3D || dyn == ROCKETS;
     if (ndim == 4) return dyn == NORMAL_SPEED || dyn == TRANSLATE || dyn == CAR4D;
     return false;
 }

@@ -26,6 +26,12 @@ static cudaError_t stage_dyn(int dyn, const StageArgs<LSP_REAL>& a, cudaStream_t
     case CAR4D:
         if constexpr (NDIM == 4) { stage_generic_kernel<4, SCHEME, CAR4D, LSP_REAL><<<nb, 256, 0, s>>>(a); break; }
         return cudaErrorInvalidValue;
+    case ROCKETS:
+        if constexpr (NDIM == 3) { stage_generic_kernel<3, SCHEME, ROCKETS, LSP_REAL><<<nb, 256, 0, s>>>(a); break; }
+        return cudaErrorInvalidValue;
+    case DOUBLE_INT:
+        if constexpr (NDIM == 2) { stage_generic_kernel<2, SCHEME, DOUBLE_INT, LSP_REAL><<<nb, 256, 0, s>>>(a); break; }
+        return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

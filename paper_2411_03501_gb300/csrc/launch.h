@@ -28,20 +28,53 @@ cudaError_t launch_stage_tiled_m(int ndim, int scheme, int dyn, const StageArgs<
 cudaError_t launch_stage_tiled(int ndim, int scheme, int dyn, const StageArgs<float>& a,
                                const Tile& t, cudaStream_t s);
 bool tile_valid(int ndim, int scheme, const Tile& t, const int* n);
+// The same stage with local coefficients / the variational clip compiled in
+// (stage_tiled_local.cu); launch_stage_tiled routes there when a asks for them.
+cudaError_t launch_stage_tiled_local(int ndim, int scheme, int dyn, const StageArgs<float>& a,
+                                     const Tile& t, cudaStream_t s);
 
 // Batched stages (batched.cu): RK2/RK3, FP32, problems of 2 to 4 dimensions.
 struct BatchProblem;
 struct BatchSegment;
 struct PersistCtl;
+// local: the problems use local dissipation coefficients or the variational
+// clip (batched_local.cu's instantiation).
 cudaError_t launch_batched(int scheme, const BatchProblem* probs, const int* block_prob, int nblocks,
-                           int step, int stage, int rk, cudaStream_t s);
+                           int step, int stage, int rk, bool local, cudaStream_t s);
+cudaError_t launch_batched_local(int scheme, const BatchProblem* probs, const int* block_prob,
+                                 int nblocks, int step, int stage, int rk, cudaStream_t s);
 // The whole batched solve as one cooperative launch of resident CTAs.
 cudaError_t launch_batched_persistent(int scheme, const BatchProblem* probs, const int* block_prob,
                                       const BatchSegment* segs, int nseg, int rk,
                                       unsigned int* done, PersistCtl* pc, Ctl* ctl,
-                                      unsigned long long wait_ns, cudaStream_t s);
+                                      unsigned long long wait_ns, bool local, cudaStream_t s);
+cudaError_t launch_batched_persistent_local(int scheme, const BatchProblem* probs,
+                                            const int* block_prob, const BatchSegment* segs,
+                                            int nseg, int rk, unsigned int* done, PersistCtl* pc,
+                                            Ctl* ctl, unsigned long long wait_ns, cudaStream_t s);
 void batch_tile_dims(int* tb, int* ta);
 bool batch_supported(int ndim, int dyn);
+
+// Implicit-surface primitives and set operations (shapes.cu).
+struct ShapeGeom {
+    int ndim;
+    int n[LSP_MAXD];
+    double lo[LSP_MAXD];
+    double h[LSP_MAXD];
+    long long npts;
+};
+enum { SHAPE_SPHERE = 0, SHAPE_BOX = 1, SHAPE_QUADRIC = 2, SHAPE_HALFSPACE = 3 };
+struct ShapeArgs {
+    int kind;
+    unsigned ignore;     // bit k set: dimension k is ignored
+    double c[LSP_MAXD];  // centre / box lower corner / quadric centre / plane point
+    double d[LSP_MAXD];  // box upper corner / quadric weights / plane normal
+    double r;            // radius / quadric offset
+};
+cudaError_t launch_shape(const ShapeGeom& g, const ShapeArgs& s, int dtype, void* out,
+                         cudaStream_t st);
+cudaError_t launch_shape_op(int op, int dtype, const void* a, const void* b, void* out,
+                            long long n, cudaStream_t st);
 
 // Adjoint of one stage (adjoint.cuh): pass A + pass B.
 template <typename R> struct AdjArgs;

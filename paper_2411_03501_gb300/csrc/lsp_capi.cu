@@ -82,8 +82,10 @@ lsp_status check_opts(const lsp_grid* g, const lsp_solve_opts* o)
     if (o->scheme < LSP_UPWIND1 || o->scheme > LSP_WENO5) return fail(LSP_EINVAL, "bad scheme");
     if (o->dtype != LSP_F32 && o->dtype != LSP_F64) return fail(LSP_EINVAL, "bad dtype");
     if (!(o->cfl > 0.0 && o->cfl <= 1.0)) return fail(LSP_EINVAL, "cfl must be in (0, 1]");
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 1; ++i)
         if (o->reserved[i]) return fail(LSP_EINVAL, "reserved option fields must be zero");
+    if (o->diss < LSP_DISS_GLF || o->diss > LSP_DISS_LLLF) return fail(LSP_EINVAL, "bad diss");
+    if (o->varform != 0 && o->varform != 1) return fail(LSP_EINVAL, "varform must be 0 or 1");
     if (o->batch_chunk < 0) return fail(LSP_EINVAL, "batch_chunk must be >= 0");
     if (o->batch_persistent != 0 && o->batch_persistent != 1)
         return fail(LSP_EINVAL, "batch_persistent must be 0 or 1");
@@ -192,6 +194,8 @@ lsp_status enqueue_stage(const lsp_grid* g, const lsp_solve_opts* o, lsp::Ctl* c
     a.c_s = R(c_s);
     a.c_l = R(c_l);
     a.tube = tube ? 1 : 0;
+    a.local_alpha = o->diss != LSP_DISS_GLF;
+    a.varform = o->varform;
     cudaError_t e;
     if (!g->alpha_state) {  // alpha from the costate range of phi_s
         e = cudaMemsetAsync(ctl->alpha_bits, 0, sizeof(ctl->alpha_bits), st);
@@ -397,6 +401,14 @@ lsp_status lsp_set_dynamics(lsp_grid* g, int dyn, const double* params, int npar
     case LSP_DYN_CAR4D:
         if (g->ndim != 4) return fail(LSP_EINVAL, "CAR4D needs a 4-D grid");
         need = 2;
+        break;
+    case LSP_DYN_ROCKETS:
+        if (g->ndim != 3) return fail(LSP_EINVAL, "ROCKETS needs a 3-D grid");
+        need = 4;
+        break;
+    case LSP_DYN_DOUBLE_INTEGRATOR:
+        if (g->ndim != 2) return fail(LSP_EINVAL, "DOUBLE_INTEGRATOR needs a 2-D grid");
+        need = 1;
         break;
     default: return fail(LSP_EINVAL, "unknown dynamics %d", dyn);
     }
@@ -895,7 +907,8 @@ lsp_status solve_batched_persistent(int nprob, const lsp_solve_opts* o,
     const unsigned long long wait_ns =
         (unsigned long long)(o->batch_wait_ms > 0 ? o->batch_wait_ms : 1000) * 1000000ULL;
     e = lsp::launch_batched_persistent(o->scheme, d_table, d_block_prob, d_segs, nseg, rk, d_done,
-                                       d_pc, ctl, wait_ns, st);
+                                       d_pc, ctl, wait_ns, o->diss != LSP_DISS_GLF || o->varform,
+                                       st);
     if (e) return cuda_fail(e, "persistent batched kernel");
     return LSP_OK;
 }
@@ -996,6 +1009,8 @@ lsp_status lsp_hj_solve_batched(int nprob, lsp_grid* const* grids, const lsp_sol
         std::memset(&P, 0, sizeof(P));
         P.a = base_args<float>(g, ctl);
         P.a.tube = o->tube ? 1 : 0;
+        P.a.local_alpha = o->diss != LSP_DISS_GLF;
+        P.a.varform = o->varform;
         P.phi = (float*)phis[e.p];
         P.target = o->tube ? (const float*)targets[e.p] : nullptr;
         P.w1 = (float*)base;
@@ -1049,7 +1064,7 @@ lsp_status lsp_hj_solve_batched(int nprob, lsp_grid* const* grids, const lsp_sol
         while (nactive > 0 && order[nactive - 1].nsteps <= k) --nactive;
         for (int stage = 0; stage < o->rk_order && !s; ++stage) {
             e = lsp::launch_batched(o->scheme, d_table, d_block_prob, prefix[nactive], k, stage,
-                                    o->rk_order, es);
+                                    o->rk_order, o->diss != LSP_DISS_GLF || o->varform, es);
             if (e) s = cuda_fail(e, "batched stage kernel");
         }
     }
@@ -1115,7 +1130,11 @@ lsp_status adj_check(const lsp_grid* g, const lsp_solve_opts* o, int nsteps)
     lsp_status s = check_opts(g, o);
     if (s) return s;
     if (!g->alpha_state) return fail(LSP_EUNSUPPORTED, "the adjoint needs state-only LF bounds");
-    if (g->dyn == LSP_DYN_QUADRATIC) return fail(LSP_EUNSUPPORTED, "no adjoint for QUADRATIC");
+    if (g->dyn == LSP_DYN_QUADRATIC || g->dyn == LSP_DYN_ROCKETS ||
+        g->dyn == LSP_DYN_DOUBLE_INTEGRATOR)
+        return fail(LSP_EUNSUPPORTED, "no adjoint for dynamics %d", g->dyn);
+    if (o->diss != LSP_DISS_GLF || o->varform)
+        return fail(LSP_EUNSUPPORTED, "the adjoint reverses the GLF form without the clip");
     if (nsteps < 1) return fail(LSP_EINVAL, "nsteps must be >= 1");
     return LSP_OK;
 }
@@ -1424,6 +1443,128 @@ lsp_status lsp_loss_tube(const lsp_grid* g, int dtype, const void* phi, const vo
         e = lsp::launch_loss<float>(L, value_dev, (float*)grad, st);
     }
     return e ? cuda_fail(e, "loss kernels") : LSP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// geometry and the shared checks of the shape primitives
+lsp_status shape_prep(const lsp_grid* g, int dtype, const void* out, unsigned ignore,
+                      lsp::ShapeGeom& geo)
+{
+    if (!g) return fail(LSP_EINVAL, "grid is NULL");
+    if (dtype != LSP_F32 && dtype != LSP_F64) return fail(LSP_EINVAL, "bad dtype");
+    if (!out) return fail(LSP_EINVAL, "out is NULL");
+    unsigned used = 0;
+    for (int k = 0; k < g->ndim; ++k)
+        if (!((ignore >> k) & 1u)) used++;
+    if (used == 0) return fail(LSP_EINVAL, "every dimension is ignored");
+    geo.ndim = g->ndim;
+    for (int k = 0; k < g->ndim; ++k) {
+        geo.n[k] = g->n[k];
+        geo.lo[k] = g->lo[k];
+        geo.h[k] = g->dx[k];
+    }
+    geo.npts = g->npts;
+    return LSP_OK;
+}
+
+lsp_status shape_run(const lsp::ShapeGeom& geo, const lsp::ShapeArgs& sa, int dtype,
+                     void* out, void* stream)
+{
+    cudaError_t e = lsp::launch_shape(geo, sa, dtype, out, (cudaStream_t)stream);
+    return e ? cuda_fail(e, "shape kernel") : LSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lsp_status lsp_shape_sphere(const lsp_grid* g, int dtype, const double* center, double radius,
+                            unsigned ignore, void* out, void* stream)
+{
+    lsp::ShapeGeom geo;
+    lsp_status s = shape_prep(g, dtype, out, ignore, geo);
+    if (s) return s;
+    if (!center) return fail(LSP_EINVAL, "center is NULL");
+    if (!(radius >= 0.0)) return fail(LSP_EINVAL, "radius must be >= 0");
+    lsp::ShapeArgs sa{};
+    sa.kind = lsp::SHAPE_SPHERE;
+    sa.ignore = ignore;
+    for (int k = 0; k < g->ndim; ++k) sa.c[k] = center[k];
+    sa.r = radius;
+    return shape_run(geo, sa, dtype, out, stream);
+}
+
+lsp_status lsp_shape_box(const lsp_grid* g, int dtype, const double* lo, const double* hi,
+                         unsigned ignore, void* out, void* stream)
+{
+    lsp::ShapeGeom geo;
+    lsp_status s = shape_prep(g, dtype, out, ignore, geo);
+    if (s) return s;
+    if (!lo || !hi) return fail(LSP_EINVAL, "lo and hi must not be NULL");
+    lsp::ShapeArgs sa{};
+    sa.kind = lsp::SHAPE_BOX;
+    sa.ignore = ignore;
+    for (int k = 0; k < g->ndim; ++k) {
+        if (!((ignore >> k) & 1u) && !(lo[k] <= hi[k]))
+            return fail(LSP_EINVAL, "box dimension %d has lo > hi", k);
+        sa.c[k] = lo[k];
+        sa.d[k] = hi[k];
+    }
+    return shape_run(geo, sa, dtype, out, stream);
+}
+
+lsp_status lsp_shape_quadric(const lsp_grid* g, int dtype, const double* center,
+                             const double* weights, double offset, unsigned ignore, void* out,
+                             void* stream)
+{
+    lsp::ShapeGeom geo;
+    lsp_status s = shape_prep(g, dtype, out, ignore, geo);
+    if (s) return s;
+    if (!center || !weights) return fail(LSP_EINVAL, "center and weights must not be NULL");
+    lsp::ShapeArgs sa{};
+    sa.kind = lsp::SHAPE_QUADRIC;
+    sa.ignore = ignore;
+    for (int k = 0; k < g->ndim; ++k) {
+        sa.c[k] = center[k];
+        sa.d[k] = weights[k];
+    }
+    sa.r = offset;
+    return shape_run(geo, sa, dtype, out, stream);
+}
+
+lsp_status lsp_shape_halfspace(const lsp_grid* g, int dtype, const double* normal,
+                               const double* point, unsigned ignore, void* out, void* stream)
+{
+    lsp::ShapeGeom geo;
+    lsp_status s = shape_prep(g, dtype, out, ignore, geo);
+    if (s) return s;
+    if (!normal || !point) return fail(LSP_EINVAL, "normal and point must not be NULL");
+    lsp::ShapeArgs sa{};
+    sa.kind = lsp::SHAPE_HALFSPACE;
+    sa.ignore = ignore;
+    double nn = 0.0;
+    for (int k = 0; k < g->ndim; ++k) {
+        sa.c[k] = point[k];
+        sa.d[k] = normal[k];
+        if (!((ignore >> k) & 1u)) nn += normal[k] * normal[k];
+    }
+    if (!(nn > 0.0)) return fail(LSP_EINVAL, "the normal is zero in the dimensions used");
+    return shape_run(geo, sa, dtype, out, stream);
+}
+
+lsp_status lsp_shape_op(int op, int dtype, const void* a, const void* b, void* out, int64_t n,
+                        void* stream)
+{
+    if (op < LSP_SHAPE_UNION || op > LSP_SHAPE_DIFFERENCE) return fail(LSP_EINVAL, "bad op");
+    if (dtype != LSP_F32 && dtype != LSP_F64) return fail(LSP_EINVAL, "bad dtype");
+    if (n < 0) return fail(LSP_EINVAL, "n must be >= 0");
+    if (n > 0 && (!a || !out || (op != LSP_SHAPE_COMPLEMENT && !b)))
+        return fail(LSP_EINVAL, "NULL field");
+    cudaError_t e = lsp::launch_shape_op(op, dtype, a, b, out, (long long)n, (cudaStream_t)stream);
+    return e ? cuda_fail(e, "shape op kernel") : LSP_OK;
 }
 
 lsp_status lsp_check_status(const void* ws, void* stream)

@@ -10,7 +10,8 @@
 namespace lsp {
 
 enum Scheme { UPWIND1 = 0, ENO2 = 1, ENO3 = 2, WENO5 = 3 };
-enum Dyn { NORMAL_SPEED = 0, TRANSLATE = 1, QUADRATIC = 2, AIR3D = 3, CAR4D = 4 };
+enum Dyn { NORMAL_SPEED = 0, TRANSLATE = 1, QUADRATIC = 2, AIR3D = 3, CAR4D = 4, ROCKETS = 5,
+           DOUBLE_INT = 6 };
 
 __host__ __device__ constexpr int ghost_width(int scheme) { return scheme == UPWIND1 ? 1 : (scheme == ENO2 ? 2 : 3); }
 
@@ -52,6 +53,8 @@ struct StageArgs {
     Ctl* ctl;            // flags; alpha/dt for p-dependent dynamics
     int alpha_from_ctl;  // 1: read alpha from ctl->alpha_bits
     int dt_from_ctl;     // 1: read dt from ctl->dt
+    int local_alpha;     // 1: LLF/LLLF coefficients per node instead of alpha[]
+    int varform;         // 1: variational form, rate clipped at zero
 };
 
 }  // namespace lsp

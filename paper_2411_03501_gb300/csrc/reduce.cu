@@ -17,6 +17,8 @@ cudaError_t launch_alpha_state(int dyn, const GridGeom& g, unsigned long long* o
     case TRANSLATE: alpha_state_kernel<TRANSLATE><<<nb, 256, 0, s>>>(g, out); break;
     case AIR3D: alpha_state_kernel<AIR3D><<<nb, 256, 0, s>>>(g, out); break;
     case CAR4D: alpha_state_kernel<CAR4D><<<nb, 256, 0, s>>>(g, out); break;
+    case ROCKETS: alpha_state_kernel<ROCKETS><<<nb, 256, 0, s>>>(g, out); break;
+    case DOUBLE_INT: alpha_state_kernel<DOUBLE_INT><<<nb, 256, 0, s>>>(g, out); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -39,6 +41,7 @@ bool tile_valid(int ndim, int scheme, const Tile& t, const int* n)
 cudaError_t launch_stage_tiled(int ndim, int scheme, int dyn, const StageArgs<float>& a,
                                const Tile& t, cudaStream_t s)
 {
+    if (a.local_alpha || a.varform) return launch_stage_tiled_local(ndim, scheme, dyn, a, t, s);
     switch (t.minb) {
     case 2: return launch_stage_tiled_m<2>(ndim, scheme, dyn, a, t, s);
     case 3: return launch_stage_tiled_m<3>(ndim, scheme, dyn, a, t, s);
@@ -67,6 +70,8 @@ bool stage_supported(int ndim, int scheme, int dyn)
     if (ndim < 1 || ndim > LSP_MAXD || scheme < UPWIND1 || scheme > WENO5) return false;
     if (dyn == AIR3D) return ndim == 3;
     if (dyn == CAR4D) return ndim == 4;
+    if (dyn == ROCKETS) return ndim == 3;
+    if (dyn == DOUBLE_INT) return ndim == 2;
     return dyn >= NORMAL_SPEED && dyn <= QUADRATIC;
 }
 

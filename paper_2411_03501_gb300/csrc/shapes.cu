@@ -1,0 +1,115 @@
+// shapes.cu -- implicit surfaces on the device (Sec. III-C: signed distance
+// primitives; Sec. III-D: calculus on implicit functions), for building
+// targets and initial fields without a host round trip.
+//
+// One thread per node (grid-stride), coordinates lo + i * dx per axis as the
+// stage kernels use them; the arithmetic is FP64 and the result is stored in
+// the field's precision.  Primitives measure distance in the non-ignored
+// dimensions only (ignoring dimensions turns a sphere into a cylinder, a box
+// into a slab); periodic axes are not wrapped.
+#include <cmath>
+
+#include "../../include/lsp.h"
+#include "launch.h"
+
+namespace lsp {
+
+__device__ __forceinline__ double shape_value(const ShapeGeom& g, const ShapeArgs& s, const double* x)
+{
+    if (s.kind == SHAPE_SPHERE) {  // |x - c| - r
+        double q = 0.0;
+        for (int k = 0; k < g.ndim; ++k)
+            if (!((s.ignore >> k) & 1u)) q += (x[k] - s.c[k]) * (x[k] - s.c[k]);
+        return sqrt(q) - s.r;
+    }
+    if (s.kind == SHAPE_BOX) {  // exact signed distance to [c, d]
+        double out2 = 0.0, in = -INFINITY;
+        for (int k = 0; k < g.ndim; ++k) {
+            if ((s.ignore >> k) & 1u) continue;
+            const double e = fmax(s.c[k] - x[k], x[k] - s.d[k]);  // > 0 outside this slab
+            if (e > 0.0) out2 += e * e;
+            in = fmax(in, e);
+        }
+        return out2 > 0.0 ? sqrt(out2) : in;
+    }
+    if (s.kind == SHAPE_QUADRIC) {  // sum_k w_k (x_k - c_k)^2 - offset
+        double q = 0.0;
+        for (int k = 0; k < g.ndim; ++k)
+            if (!((s.ignore >> k) & 1u)) q += s.d[k] * (x[k] - s.c[k]) * (x[k] - s.c[k]);
+        return q - s.r;
+    }
+    // half space {n . (x - p) <= 0}: signed distance n . (x - p) / |n|
+    double q = 0.0, nn = 0.0;
+    for (int k = 0; k < g.ndim; ++k)
+        if (!((s.ignore >> k) & 1u)) {
+            q += s.d[k] * (x[k] - s.c[k]);
+            nn += s.d[k] * s.d[k];
+        }
+    return q / sqrt(nn);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) shape_kernel(ShapeGeom g, ShapeArgs s, R* out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.npts;
+         i += (long long)gridDim.x * blockDim.x) {
+        double x[LSP_MAXD];
+        long long r = i;
+        for (int k = g.ndim - 1; k >= 0; --k) {
+            x[k] = g.lo[k] + double(r % g.n[k]) * g.h[k];
+            r /= g.n[k];
+        }
+        out[i] = R(shape_value(g, s, x));
+    }
+}
+
+// union min(a, b), intersection max(a, b), complement -a, difference
+// max(a, -b) (Sec. III-D)
+template <typename R>
+__global__ void __launch_bounds__(256) shape_op_kernel(int op, const R* a, const R* b, R* out,
+                                                       long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const R u = a[i];
+        R v;
+        switch (op) {
+        case LSP_SHAPE_UNION: v = fmin(u, b[i]); break;
+        case LSP_SHAPE_INTERSECT: v = fmax(u, b[i]); break;
+        case LSP_SHAPE_COMPLEMENT: v = -u; break;
+        default: v = fmax(u, -b[i]); break;
+        }
+        out[i] = v;
+    }
+}
+
+static int shape_blocks(long long n)
+{
+    const long long b = (n + 255) / 256;
+    return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+cudaError_t launch_shape(const ShapeGeom& g, const ShapeArgs& s, int dtype, void* out,
+                         cudaStream_t st)
+{
+    if (dtype == LSP_F64)
+        shape_kernel<double><<<shape_blocks(g.npts), 256, 0, st>>>(g, s, (double*)out);
+    else
+        shape_kernel<float><<<shape_blocks(g.npts), 256, 0, st>>>(g, s, (float*)out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shape_op(int op, int dtype, const void* a, const void* b, void* out, long long n,
+                            cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (dtype == LSP_F64)
+        shape_op_kernel<double><<<shape_blocks(n), 256, 0, st>>>(op, (const double*)a,
+                                                                 (const double*)b, (double*)out, n);
+    else
+        shape_op_kernel<float><<<shape_blocks(n), 256, 0, st>>>(op, (const float*)a,
+                                                               (const float*)b, (float*)out, n);
+    return cudaGetLastError();
+}
+
+}  // namespace lsp

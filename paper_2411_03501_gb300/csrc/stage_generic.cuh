@@ -5,8 +5,9 @@
 //   out = c_n phi^n + c_s phi_s + c_l dt L(phi_s),  L = -Hhat (Sec. IV-D)
 // with, per node: ghost substitution (Sec. III-B), left/right derivatives
 // along every axis (Sec. IV), the Hamiltonian at the average costate and the
-// global-LF dissipation sum_k alpha_k (p+_k - p-_k)/2, then (last stage of a
-// tube step) the minimum with the target (Sec. VI-A).  Stencil reads go
+// Lax-Friedrichs dissipation sum_k alpha_k (p+_k - p-_k)/2 (global or local
+// coefficients), the rate clipped at zero in the variational form, then
+// (last stage of a tube step) the minimum with the target (Sec. VI-A).  Stencil reads go
 // through the read-only cache; each node is written once.
 #pragma once
 #include "stencil.cuh"
@@ -37,6 +38,11 @@ __global__ void __launch_bounds__(256) stage_generic_kernel(StageArgs<R> a)
             }
         }
         R x[NDIM], pbar[NDIM];
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) x[k] = a.lo[k] + R(c[k]) * a.h[k];
+        R sth = R(0), cth = R(1);  // heading, for the local coefficients
+        if constexpr (DYN == AIR3D || DYN == CAR4D || DYN == ROCKETS)
+            if (a.local_alpha) rsincos(x[2], &sth, &cth);
         R diss = R(0);
 #pragma unroll
         for (int k = 0; k < NDIM; ++k) {
@@ -45,11 +51,12 @@ __global__ void __launch_bounds__(256) stage_generic_kernel(StageArgs<R> a)
             R pm, pp;
             deriv<SCHEME>(u, a.inv_dx[k], pm, pp);
             pbar[k] = R(0.5) * (pp + pm);
-            diss += alpha[k] * R(0.5) * (pp - pm);
-            x[k] = a.lo[k] + R(c[k]) * a.h[k];
+            const R ak = a.local_alpha ? local_alpha<DYN>(x, k, a.prm, sth, cth, pm, pp) : alpha[k];
+            diss += ak * R(0.5) * (pp - pm);
         }
         const R H = hamiltonian<DYN, NDIM>(x, pbar, a.prm);
-        const R L = -(H - diss);
+        R L = -(H - diss);
+        if (a.varform) L = rmin(L, R(0));
         R v = a.c_s * __ldg(a.phi_s + idx) + cl * L;
         if (a.phi_n) v += a.c_n * a.phi_n[idx];
         if (a.tube) v = rmin(v, __ldg(a.target + idx));

@@ -37,7 +37,15 @@ __device__ __forceinline__ F2 hamiltonian_pair(const F2* x, const F2* p, const f
         const F2 m = p[0] * x[3] * F2(c) + p[1] * x[3] * F2(s) - F2(prm[0]) * abs2(p[2]) -
                      F2(prm[1]) * abs2(p[3]);
         return -m;
+    } else if constexpr (DYN == ROCKETS) {  // hamiltonian_rockets for two nodes
+        const float a = prm[0], ue = prm[2], up = prm[3];
+        const F2 fx(a * c), fz(fmaf(a, s, a - prm[1]));
+        F2 v = fma2(p[0], fx, p[1] * fz);
+        v = fma2(F2(ue), abs2(fma2(p[0], x[0], -p[2])), v);
+        v = fma2(F2(-up), abs2(fma2(p[1], x[0], p[2])), v);
+        return -v;
     } else {
+        static_assert(DYN == QUADRATIC, "no paired Hamiltonian for these dynamics");
         F2 n2 = p[0] * p[0];
 #pragma unroll
         for (int k = 1; k < NDIM; ++k) n2 = fma2(p[k], p[k], n2);
@@ -84,7 +92,7 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
     x[AA] = F2(a.lo[AA] + float(ia) * a.h[AA]);
     x[AB] = F2(a.lo[AB] + float(ib) * a.h[AB]);
     float sth = 0.f, cth = 1.f;
-    if constexpr (DYN == AIR3D || DYN == CAR4D) sincosf(x[2].x(), &sth, &cth);
+    if constexpr (DYN == AIR3D || DYN == CAR4D || DYN == ROCKETS) sincosf(x[2].x(), &sth, &cth);
 
     const int ia_c = min(ia, nA - 1), ib_c = min(ib, nB - 1);
     const float* col = a.phi_s + base_outer + ia_c * sA + ib_c;

@@ -132,7 +132,12 @@ struct Tile {
 // chunk `chunk` of the march along axis S and, for 4-D grids, index `outer`
 // along axis 0.  2-D grids have no march (one plane).  Block of TB x TA
 // threads (tx, ty); `tile` holds (TA + 2G) x (TB + 2G) values.
-template <int NDIM, int SCHEME, int DYN, typename R, bool COH = false>
+// LOCAL = true compiles the per-node dissipation coefficients (LLF/LLLF) and
+// the variational clip in, each taken when its StageArgs flag is set;
+// LOCAL = false is the global-LF form alone (the code the benchmark runs,
+// kept free of the local variants so that every kernel that inlines it
+// rounds it the same way).
+template <int NDIM, int SCHEME, int DYN, typename R, bool COH = false, bool LOCAL = false>
 __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, int TA, int bx,
                                                  int by, int chunk, int outer, int ch, R* tile,
                                                  int tx, int ty)
@@ -168,11 +173,11 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
     // coordinates fixed for this thread (and the heading's sin/cos: theta
     // is axis 2, one of the tile axes, for both 3-D and 4-D games)
     R x[NDIM];
-    if constexpr (NDIM == 4) x[0] = a.lo[0] + R(outer) * a.h[0];
-    x[AA] = a.lo[AA] + R(ia) * a.h[AA];
-    x[AB] = a.lo[AB] + R(ib) * a.h[AB];
+    if constexpr (NDIM == 4) x[0] = rfma(R(outer), a.h[0], a.lo[0]);
+    x[AA] = rfma(R(ia), a.h[AA], a.lo[AA]);
+    x[AB] = rfma(R(ib), a.h[AB], a.lo[AB]);
     R sth = R(0), cth = R(1);
-    if constexpr (DYN == AIR3D || DYN == CAR4D) rsincos(x[2], &sth, &cth);
+    if constexpr (DYN == AIR3D || DYN == CAR4D || DYN == ROCKETS) rsincos(x[2], &sth, &cth);
 
     // own column along S (clamped so inactive threads stay in bounds)
     const int ia_c = min(ia, nA - 1), ib_c = min(ib, nB - 1);
@@ -258,10 +263,18 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
         if (active) {
             const R* tile = tile_s;
             R pm, pp, pbar[NDIM], diss = R(0);
+            if constexpr (HAS_S) x[AS] = rfma(R(s), a.h[AS], a.lo[AS]);
+            // dissipation coefficient of axis k: global, or local (LLF/LLLF)
+            auto coef = [&](int k, R m, R p) -> R {
+                if constexpr (LOCAL)
+                    return a.local_alpha ? local_alpha<DYN>(x, k, a.prm, sth, cth, m, p) : alpha[k];
+                else
+                    return alpha[k];
+            };
             if constexpr (HAS_S) {  // S axis from the register window
                 deriv_fast<SCHEME>(w, a.inv_dx[AS], weno_floor12(a.inv_dx[AS]), pm, pp);
                 pbar[AS] = R(0.5) * (pp + pm);
-                diss += alpha[AS] * R(0.5) * (pp - pm);
+                diss = rfma(coef(AS, pm, pp) * R(0.5), pp - pm, diss);
             }
             {  // A axis from the tile column
                 R u[2 * G + 1];
@@ -269,7 +282,7 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
                 for (int o = 0; o <= 2 * G; ++o) u[o] = tile[(ty + o) * W + tx + G];
                 deriv_fast<SCHEME>(u, a.inv_dx[AA], fl_a, pm, pp);
                 pbar[AA] = R(0.5) * (pp + pm);
-                diss += alpha[AA] * R(0.5) * (pp - pm);
+                diss = rfma(coef(AA, pm, pp) * R(0.5), pp - pm, diss);
             }
             R center;
             {  // B axis from the tile row
@@ -279,7 +292,7 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
                 center = u[G];
                 deriv_fast<SCHEME>(u, a.inv_dx[AB], fl_b, pm, pp);
                 pbar[AB] = R(0.5) * (pp + pm);
-                diss += alpha[AB] * R(0.5) * (pp - pm);
+                diss = rfma(coef(AB, pm, pp) * R(0.5), pp - pm, diss);
             }
             if constexpr (NDIM == 4) {
                 // axis 0 (a grid dimension): window straight from global memory
@@ -297,14 +310,15 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
                 }
                 deriv_fast<SCHEME>(u, a.inv_dx[0], weno_floor12(a.inv_dx[0]), pm, pp);
                 pbar[0] = R(0.5) * (pp + pm);
-                diss += alpha[0] * R(0.5) * (pp - pm);
+                diss = rfma(coef(0, pm, pp) * R(0.5), pp - pm, diss);
             }
-            if constexpr (HAS_S) x[AS] = a.lo[AS] + R(s) * a.h[AS];
             const R Hv = hamiltonian_sc<DYN, NDIM>(x, pbar, a.prm, sth, cth);
-            const R L = -(Hv - diss);
+            R L = -(Hv - diss);
+            if constexpr (LOCAL)
+                if (a.varform) L = rmin(L, R(0));
             const int idx = base_outer + s * sS + ia * sA + ib;
-            R v = a.c_s * center + cl * L;
-            if (a.phi_n) v += a.c_n * (COH ? __ldcg(a.phi_n + idx) : a.phi_n[idx]);
+            R v = rfma(cl, L, a.c_s * center);
+            if (a.phi_n) v = rfma(a.c_n, COH ? __ldcg(a.phi_n + idx) : a.phi_n[idx], v);
             if (a.tube) v = rmin(v, __ldg(a.target + idx));
             nonfinite |= !isfinite(v);
             a.out[idx] = v;
@@ -321,12 +335,12 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
 // ceil(nA/ta), nchunks * nOuter).
 // MINB: CTAs of 256 threads that must fit on one SM (2: up to 128
 // registers per thread, 3: 80, 4: 64).
-template <int NDIM, int SCHEME, int DYN, typename R, int MINB>
+template <int NDIM, int SCHEME, int DYN, typename R, int MINB, bool LOCAL = false>
 __global__ void __launch_bounds__(256, MINB) stage_tiled_kernel(StageArgs<R> a, int ch, int nchunks)
 {
     extern __shared__ unsigned char smem_raw[];
     R* tile = reinterpret_cast<R*>(smem_raw);
-    tiled_stage_body<NDIM, SCHEME, DYN, R>(a, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y,
+    tiled_stage_body<NDIM, SCHEME, DYN, R, false, LOCAL>(a, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y,
                                            blockIdx.z % nchunks, blockIdx.z / nchunks, ch, tile,
                                            threadIdx.x, threadIdx.y);
 }

@@ -16,6 +16,8 @@ static cudaError_t tiled_one(const StageArgs<float>& a, const Tile& t, cudaStrea
     dim3 grid((nB + t.tb - 1) / t.tb, (nA + t.ta - 1) / t.ta,
               nchunks * (NDIM == 4 ? a.n[0] : 1));
     const size_t smem = 2 * sizeof(float) * (t.ta + 2 * G) * (t.tb + 2 * G);
+    // (local coefficients and the variational clip never reach this file:
+    // launch_stage_tiled sends them to stage_tiled_local.cu)
     if constexpr (SCHEME == WENO5) {
         if (t.pair == 1) {
             stage_pair_kernel<NDIM, DYN, LSP_MINB, false><<<grid, block, 2 * smem, s>>>(a, t.ch, nchunks);
@@ -42,6 +44,9 @@ static cudaError_t tiled_dyn(int dyn, const StageArgs<float>& a, const Tile& t, 
         break;
     case CAR4D:
         if constexpr (NDIM == 4) return tiled_one<4, SCHEME, CAR4D>(a, t, s);
+        break;
+    case ROCKETS:
+        if constexpr (NDIM == 3) return tiled_one<3, SCHEME, ROCKETS>(a, t, s);
         break;
     }
     return cudaErrorInvalidValue;

@@ -33,6 +33,10 @@ template <> struct Num<double> {
 };
 
 __device__ __forceinline__ float rabs(float x) { return fabsf(x); }
+// explicit fused multiply-add: the same rounding in every kernel that inlines
+// the caller, whatever the compiler would contract there
+__device__ __forceinline__ float rfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ double rabs(double x) { return fabs(x); }
 __device__ __forceinline__ float rmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double rmax(double a, double b) { return fmax(a, b); }
@@ -148,6 +152,25 @@ __device__ __forceinline__ void deriv(const R* u, R inv_dx, R& pm, R& pp)
 }
 
 // ---------------------------------------------------------------------------
+// Rockets game (Sec. VI-A, Eq. 31): f = (a cos th + u_e x, a sin th + a +
+// u_p x - g, u_p - u_e), evader u_e in [-ue, ue] maximises, pursuer u_p in
+// [-up, up] minimises, H = -max min p.f; with p.f = p1 a cos th +
+// p2 (a sin th + a - g) + u_e (p1 x - p3) + u_p (p2 x + p3) the optimum is
+// p1 a cos th + p2 (a sin th + a - g) + ue |p1 x - p3| - up |p2 x + p3|.
+// (Eq. 32 prints this closed form with three sign slips; the definition is
+// what is evaluated.)  Explicit operations: see hamiltonian_sc.
+template <typename R>
+__device__ __forceinline__ R hamiltonian_rockets(const R* x, const R* p, const R* prm, R s, R c)
+{
+    const R a = prm[0], g = prm[1], ue = prm[2], up = prm[3];
+    const R fx = a * c, fz = rfma(a, s, a - g);
+    R v = rfma(p[0], fx, p[1] * fz);
+    v = rfma(ue, rabs(rfma(p[0], x[0], -p[2])), v);
+    v = rfma(-up, rabs(rfma(p[1], x[0], p[2])), v);
+    return -v;
+}
+
+// ---------------------------------------------------------------------------
 // Hamiltonians at (x, p).  Reachability games follow H = -max_u min_d p.f
 // (Sec. VI-A, Eq. 31) evaluated in closed form: the optimal bounded inputs
 // are picked by the sign of their costate coefficient, which produces the
@@ -180,32 +203,83 @@ __device__ __forceinline__ R hamiltonian(const R* x, const R* p, const R* prm)
         const R v = p[0] * (-ve + vp * c) + p[1] * (vp * s) +
                     um * rabs(p[0] * x[1] - p[1] * x[0] - p[2]) - dm * rabs(p[2]);
         return -v;
-    } else {  // CAR4D: xdot = v cos th, ydot = v sin th, thdot = w, vdot = a;
-              // both inputs minimise p.f (reach).
+    } else if constexpr (DYN == CAR4D) {  // xdot = v cos th, ydot = v sin th, thdot = w,
+                                         // vdot = a; both inputs minimise p.f (reach)
         R s, c;
         rsincos(x[2], &s, &c);
         const R v = x[3];
         const R m = p[0] * v * c + p[1] * v * s - prm[0] * rabs(p[2]) - prm[1] * rabs(p[3]);
         return -m;
+    } else if constexpr (DYN == ROCKETS) {
+        R s, c;
+        rsincos(x[2], &s, &c);
+        return hamiltonian_rockets(x, p, prm, s, c);
+    } else {  // DOUBLE_INT: x1dot = x2, x2dot = u, |u| <= umax minimises p.f (reach)
+        return -rfma(p[0], x[1], -prm[0] * rabs(p[1]));
     }
 }
 
 // Hamiltonian with the coordinate-only factors (sin/cos of the heading)
 // precomputed by the caller: hamiltonian_sc(x, p, prm, sin th, cos th).
+// Every product and sum is an explicit operation here (and in local_alpha
+// below, which shares factors with it), so the rounding does not depend on
+// how the compiler fuses them in the kernel that inlines the call: the tiled
+// body gives the same bits in the single-problem and the batched kernels.
 template <int DYN, int NDIM, typename R>
 __device__ __forceinline__ R hamiltonian_sc(const R* x, const R* p, const R* prm, R s, R c)
 {
     if constexpr (DYN == AIR3D) {
         const R ve = prm[0], vp = prm[1], um = prm[2], dm = prm[3];
-        const R v = p[0] * (-ve + vp * c) + p[1] * (vp * s) +
-                    um * rabs(p[0] * x[1] - p[1] * x[0] - p[2]) - dm * rabs(p[2]);
+        const R fx = rfma(vp, c, -ve);  // -v_e + v_p cos th
+        const R fy = vp * s;
+        const R sw = rfma(p[0], x[1], -(p[1] * x[0])) - p[2];
+        R v = rfma(p[0], fx, p[1] * fy);
+        v = rfma(um, rabs(sw), v);
+        v = rfma(-dm, rabs(p[2]), v);
         return -v;
     } else if constexpr (DYN == CAR4D) {
-        const R v = x[3];
-        const R m = p[0] * v * c + p[1] * v * s - prm[0] * rabs(p[2]) - prm[1] * rabs(p[3]);
+        const R vc = x[3] * c, vs = x[3] * s;
+        R m = rfma(p[0], vc, p[1] * vs);
+        m = rfma(-prm[0], rabs(p[2]), m);
+        m = rfma(-prm[1], rabs(p[3]), m);
         return -m;
+    } else if constexpr (DYN == ROCKETS) {
+        return hamiltonian_rockets(x, p, prm, s, c);
     } else {
         return hamiltonian<DYN, NDIM>(x, p, prm);
+    }
+}
+
+// Local dissipation coefficient of axis k at one node (LLF / LLLF, Sec.
+// IV-D's Lax-Friedrichs term with the toolbox's local siblings of the GLF
+// routine): the bound on |dH/dp_k| at the node's state, or for H = |p|^2/2
+// over the node's own costate interval, max(|p-_k|, |p+_k|).  The bounds
+// involve at most the costate of axis k, so LLF and LLLF coincide.  s, c:
+// sin and cos of the heading x[2] (AIR3D, CAR4D).
+template <int DYN, typename R>
+__device__ __forceinline__ R local_alpha(const R* x, int k, const R* prm, R s, R c, R pm, R pp)
+{
+    if constexpr (DYN == NORMAL_SPEED) {
+        return rabs(prm[0]);
+    } else if constexpr (DYN == TRANSLATE) {
+        return rabs(prm[k]);
+    } else if constexpr (DYN == QUADRATIC) {
+        return rmax(rabs(pm), rabs(pp));
+    } else if constexpr (DYN == AIR3D) {
+        if (k == 0) return rfma(prm[2], rabs(x[1]), rabs(rfma(prm[1], c, -prm[0])));
+        if (k == 1) return rfma(prm[2], rabs(x[0]), prm[1] * rabs(s));
+        return prm[2] + prm[3];
+    } else if constexpr (DYN == CAR4D) {
+        if (k == 0) return rabs(x[3] * c);
+        if (k == 1) return rabs(x[3] * s);
+        if (k == 2) return prm[0];
+        return prm[1];
+    } else if constexpr (DYN == ROCKETS) {
+        if (k == 0) return rfma(prm[2], rabs(x[0]), rabs(prm[0] * c));
+        if (k == 1) return rfma(prm[3], rabs(x[0]), rabs(rfma(prm[0], s, prm[0] - prm[1])));
+        return prm[2] + prm[3];
+    } else {  // DOUBLE_INT
+        return k == 0 ? rabs(x[1]) : rabs(prm[0]);
     }
 }
 
@@ -231,6 +305,14 @@ __device__ __forceinline__ double partial_bound(const double* x, int k, const do
         if (k == 1) return fabs(x[3] * s);
         if (k == 2) return prm[0];
         return prm[1];
+    } else if constexpr (DYN == ROCKETS) {
+        double s, c;
+        sincos(x[2], &s, &c);
+        if (k == 0) return prm[0] * fabs(c) + prm[2] * fabs(x[0]);
+        if (k == 1) return fabs(prm[0] * s + prm[0] - prm[1]) + prm[3] * fabs(x[0]);
+        return prm[2] + prm[3];
+    } else if constexpr (DYN == DOUBLE_INT) {
+        return k == 0 ? fabs(x[1]) : fabs(prm[0]);
     } else {
         return 0.0;
     }

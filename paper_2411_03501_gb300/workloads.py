@@ -19,6 +19,13 @@ axis) since the paper ships no dataset:
 * ``car4d``: car (x, y, theta, v), |turn rate| <= 1, |acceleration| <= 1,
   disc target of radius 0.5, x, y in [-4, 4], v in [0, 2], 81^4 nodes, ENO3,
   RK3, CFL 0.75, t_final 1.0, FP32, reachable tube.
+* ``rockets``: the two-rocket game of Sec. VI-A (x, z, theta), a = 1,
+  g = 32, input bounds 1, cylinder target of capture radius 1.5 along theta,
+  100^3 nodes, x, z in [-64, 64], theta in [-pi/2, pi/2] (extrapolated),
+  ENO2 (Listing 5), RK2, CFL 0.75, t_final 2.5, FP32, reachable tube.
+* ``double_integrator``: x1dot = x2, x2dot = u, |u| <= 1, disc target of
+  radius 0.1 on [-1, 1]^2, 101^2 nodes, ENO2, RK2, CFL 0.75, t_final 1.0,
+  FP64, reachable tube.
 * ``batched``: 256 independent problems, half 2-D normal-speed, half 3-D
   air3d-style, sides, speeds and radii drawn from numpy's default_rng with
   seed 20241105 (side, speed, radius per problem, in that order).
@@ -151,6 +158,27 @@ def car4d(n: int = 81, wmax: float = 1.0, amax: float = 1.0, radius: float = 0.5
     return spec, g.copy(), g
 
 
+def rockets(n: int = 100, a: float = 1.0, g: float = 32.0, ue: float = 1.0, up: float = 1.0,
+            radius: float = 1.5, t_final: float = 2.5, scheme: str = "eno2", dtype: str = "f32"):
+    """The rockets game of Sec. VI-A on the paper's grid (100 nodes per axis,
+    [-64, 64] for x and z; theta over its stated range [-pi/2, pi/2])."""
+    spec = problem(3, [n, n, n], [-64, -64, -math.pi / 2], [64, 64, math.pi / 2],
+                   [False, False, False], scheme, "rockets", [a, g, ue, up], rk=2, cfl=0.75,
+                   t_final=t_final, dtype=dtype, tube=True,
+                   name=f"rockets_{n}^3_{scheme}_rk2_{dtype}")
+    tgt = circle_sdf(spec, radius)
+    return spec, tgt.copy(), tgt
+
+
+def double_integrator(n: int = 101, umax: float = 1.0, radius: float = 0.1,
+                      t_final: float = 1.0, scheme: str = "eno2", dtype: str = "f64"):
+    spec = problem(2, [n, n], [-1, -1], [1, 1], [False, False], scheme, "double_integrator",
+                   [umax], rk=2, cfl=0.75, t_final=t_final, dtype=dtype, tube=True,
+                   name=f"double_integrator_{n}^2_{scheme}_rk2_{dtype}")
+    tgt = circle_sdf(spec, radius)
+    return spec, tgt.copy(), tgt
+
+
 def batched(count: int = 256, seed: int = 20241105, scale: float = 1.0):
     """The batched workload: ``count`` problems, the first half 2-D normal-speed
     expansions on [-1, 1]^2 (side ~ U{64..256}, speed ~ U[2, 6], radius ~
@@ -191,4 +219,6 @@ CONFIGS = {
     "normal_speed_2d": normal_speed_2d,
     "air3d": air3d,
     "car4d": car4d,
+    "rockets": rockets,
+    "double_integrator": double_integrator,
 }

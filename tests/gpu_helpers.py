@@ -126,6 +126,24 @@ def noise_spread(spec, phi0, target, t_final, ref, samples=2, rel=6e-8, seed=0):
     return worst
 
 
+def adjoint_noise_spread(spec, phi0, g, nsteps, rk, lamT, ref0, ref_g, samples=3, rel=6e-8,
+                         seed=0):
+    """How far the FP64 oracle's adjoint (lam0, lam_target) moves when phi0 and
+    lamT carry independent relative noise of FP32 size: the conditioning of
+    the discrete adjoint (WENO weight derivatives, the regulariser's argmax,
+    near-tied selections) at FP32 precision.  Returns (spread_lam0,
+    spread_lam_target)."""
+    rng = np.random.default_rng(seed)
+    w0 = wg = 0.0
+    for _ in range(samples):
+        p = phi0 * (1.0 + rel * rng.standard_normal(phi0.shape))
+        lt = lamT * (1.0 + rel * rng.standard_normal(lamT.shape))
+        a0, ag, _, _ = oracle.adjoint(spec, p, nsteps, rk, spec["cfl"], lt, target=g)
+        w0 = max(w0, float(np.abs(a0 - ref0).max()))
+        wg = max(wg, float(np.abs(ag - ref_g).max()))
+    return w0, wg
+
+
 def check_fp32_solve(got, want, spread, scale_bar=1e-4, factor=3.0):
     """The FP32 precision bar for whole solves: max|got - want| <= max(
     scale_bar * max|want|, factor * spread), spread from noise_spread.  The

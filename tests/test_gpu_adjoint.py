@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_helpers import rounded, to_dev
+from gpu_helpers import adjoint_noise_spread, rounded, to_dev
 from paper_2411_03501_gb300 import binding as B
 from paper_2411_03501_gb300 import workloads as W
 from paper_2411_03501_gb300.autograd import HJTube
@@ -74,12 +74,19 @@ def test_fp64_adjoint_matches_oracle(kind, scheme, rk):
 
 @pytest.mark.parametrize("kind,scheme,rk", CASES[:2] + CASES[4:])
 def test_fp32_adjoint_matches_oracle(kind, scheme, rk):
+    """FP32 adjoint against the FP64 oracle with the bar of the FP32 solves:
+    max(1e-4 max|lam|, 3 x the oracle's own spread under FP32-sized input
+    noise) -- the WENO5 air3d adjoint is conditioned so that the FP64 oracle
+    itself moves by ~2e-4 relative under such noise."""
     spec, phi0, g, nsteps = _case(kind, scheme, "f32", rk)
     lamT = rounded(np.random.default_rng(4).standard_normal(spec["n"]), "f32")
     _, lam0, lamg, dprm = _gpu_adjoint(spec, phi0, g, nsteps, lamT)
     o0, og, oprm, _ = oracle.adjoint(spec, phi0, nsteps, rk, spec["cfl"], lamT, target=g)
-    assert np.abs(lam0 - o0).max() <= 1e-4 * np.abs(o0).max(), np.abs(lam0 - o0).max()
-    assert np.abs(lamg - og).max() <= 1e-4 * max(np.abs(og).max(), 1e-30)
+    s0, sg = adjoint_noise_spread(spec, phi0, g, nsteps, rk, lamT, o0, og)
+    bar0 = max(1e-4 * np.abs(o0).max(), 3.0 * s0)
+    barg = max(1e-4 * max(np.abs(og).max(), 1e-30), 3.0 * sg)
+    assert np.abs(lam0 - o0).max() <= bar0, (np.abs(lam0 - o0).max(), bar0)
+    assert np.abs(lamg - og).max() <= barg, (np.abs(lamg - og).max(), barg)
     npar = len(spec["params"])
     floor = 1e-4 * max(np.abs(oprm).max(), np.abs(o0).max())
     np.testing.assert_allclose(dprm[:npar], oprm[:npar], rtol=1e-3, atol=floor)

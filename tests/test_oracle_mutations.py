@@ -60,6 +60,13 @@ MUTANTS = {
     "air3d_cos_sin": ("p[0] * (-ve + vp * cos(th))", "p[0] * (-ve + vp * sin(th))"),
     "car4d_bound_axis": ("if (k == 1) return fabs(x[3] * sin(x[2]));",
                          "if (k == 1) return fabs(x[3] * cos(x[2]));"),
+    # the switching term as Eq. 32 prints it (the reading derives it from Eq. 31)
+    "rockets_switch_as_printed": ("ue * fabs(p[0] * X - p[2])", "ue * fabs(p[0] * X + p[2])"),
+    "rockets_gravity_sign": ("p[1] * (a * sin(th) + a - g)", "p[1] * (a * sin(th) + a + g)"),
+    "rockets_bound_axis": ("if (k == 0) return a * fabs(cos(x[2])) + ue * fabs(x[0]);",
+                           "if (k == 0) return a * fabs(cos(x[2])) + ue * fabs(x[1]);"),
+    "double_integrator_input_sign": ("return -(p[0] * x[1] - um * fabs(p[1]));",
+                                     "return -(p[0] * x[1] + um * fabs(p[1]));"),
 }
 
 # mistakes in the discrete adjoint, caught by the finite-difference pins

@@ -452,3 +452,88 @@ def test_air3d_tube_invariants(orc):
     mirrored = mirrored[:, :, (-np.arange(n[2])) % n[2]]
     assert np.abs(phi - mirrored).max() < 1e-9
     assert vol_prev > (g <= 0).sum()
+
+
+# --------------------------------------------------------------- more dynamics
+def _rockets_f(x, ue, up, a, g):
+    X, Z, th = x
+    return np.array([a * np.cos(th) + ue * X, a * np.sin(th) + a + up * X - g, up - ue])
+
+
+def test_rockets_hamiltonian_is_maxmin_of_eq31_dynamics(orc):
+    """Sec. VI-A, Eq. 31: H = -max_{u_e} min_{u_p} p.f with the dynamics the
+    equation displays (a_e = a_p = a), by brute force over the input boxes;
+    the evader maximises, the pursuer minimises."""
+    spec = W.rockets(n=9)[0]
+    a, g, ue, up = spec["params"]
+    rng = np.random.default_rng(13)
+    ues = np.linspace(-ue, ue, 41)
+    ups = np.linspace(-up, up, 41)
+    for _ in range(50):
+        x = np.array([rng.uniform(-64, 64), rng.uniform(-64, 64), rng.uniform(-1.5, 1.5)])
+        p = rng.standard_normal(3)
+        best = max(min(p @ _rockets_f(x, e, q, a, g) for q in ups) for e in ues)
+        assert abs(orc.ham(spec, x, p) - (-best)) < 1e-12 * (1 + abs(best))
+
+
+def test_double_integrator_hamiltonian_is_min_of_dynamics(orc):
+    """Reach: the input minimises p.f over |u| <= umax."""
+    spec = W.double_integrator(n=9)[0]
+    um = spec["params"][0]
+    rng = np.random.default_rng(14)
+    us = np.linspace(-um, um, 41)
+    for _ in range(50):
+        x = rng.uniform(-1, 1, 2)
+        p = rng.standard_normal(2)
+        best = min(p @ np.array([x[1], u]) for u in us)
+        assert abs(orc.ham(spec, x, p) - (-best)) < 1e-12 * (1 + abs(best))
+
+
+@pytest.mark.parametrize("maker", ["rockets", "double_integrator"])
+def test_partial_bounds_dominate_and_are_tight_new_dynamics(orc, maker):
+    spec = W.rockets(n=9)[0] if maker == "rockets" else W.double_integrator(n=9)[0]
+    d = spec["ndim"]
+    rng = np.random.default_rng(15)
+    h = 1e-6
+    for _ in range(20):
+        x = np.array([rng.uniform(spec["lo"][k], spec["hi"][k]) for k in range(d)])
+        best = np.zeros(d)
+        for _ in range(200):
+            p = rng.standard_normal(d)
+            for k in range(d):
+                e = np.zeros(d)
+                e[k] = h
+                gk = (orc.ham(spec, x, p + e) - orc.ham(spec, x, p - e)) / (2 * h)
+                assert abs(gk) <= orc.partial_bound(spec, x, k) + 1e-6 * (1 + abs(gk))
+                best[k] = max(best[k], abs(gk))
+        for k in range(d):
+            assert best[k] >= orc.partial_bound(spec, x, k) * 0.8
+
+
+def _double_integrator_time(x1, x2):
+    """Minimum time to the origin for x1dot = x2, x2dot = u, |u| <= 1
+    (bang-bang with one switch on the curve x1 = -x2|x2|/2)."""
+    above = x1 > -x2 * np.abs(x2) / 2
+    ta = x2 + 2 * np.sqrt(np.maximum(x1 + x2 ** 2 / 2, 0.0))
+    tb = -x2 + 2 * np.sqrt(np.maximum(-x1 + x2 ** 2 / 2, 0.0))
+    return np.where(above, ta, tb)
+
+
+def test_double_integrator_tube_is_the_minimum_time_sublevel_set(orc):
+    """The reachable tube of a small disc D around the origin after time t
+    brackets {T <= t}, T the closed-form minimum time to the origin: since
+    T(x) <= T_D(x) + max_{y in D} T(y) (reach D, then the origin) and
+    T_D <= T, nodes with T < t - m are in the computed tube and nodes with
+    T > t + max_D T + m are not; m covers the grid's numerical diffusion."""
+    spec, phi0, g = W.double_integrator(n=81, radius=0.05, t_final=0.6)
+    phi, _ = orc.solve(spec, phi0, 0.6, 2, 0.75, target=g)
+    xs = W.mesh(spec)
+    T = _double_integrator_time(xs[0], xs[1])
+    ang = np.linspace(0, 2 * np.pi, 721)
+    rad = np.linspace(0, 0.05, 51)[:, None]
+    tmax_disc = _double_integrator_time(rad * np.cos(ang), rad * np.sin(ang)).max()
+    m = 0.1
+    inside, outside = T < 0.6 - m, T > 0.6 + tmax_disc + m
+    assert np.all(phi[inside] <= 0)
+    assert np.all(phi[outside] > 0)
+    assert inside.sum() > 50 and outside.sum() > 1000
