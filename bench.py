@@ -170,6 +170,28 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def roofline_of(flops: float, nbytes: float, seconds: float, traffic):
+    """Roofline object of a kernel that does `flops` algorithmic FLOPs and
+    moves `nbytes` algorithmic bytes per launch in `seconds`: the FP32 ALU
+    roof (152 SMs x 128 lanes x 2 x max SM clock) and the measured HBM copy
+    roof; the binding one (larger fraction) first, the other inside."""
+    peaks, src = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    hbm_peak = float(peaks["hbm_gbs"])
+    flop_ach = flops / seconds / 1e12
+    hbm_ach = nbytes / seconds / 1e9
+    alu = {"bound": "alu", "achieved": flop_ach, "peak": alu_peak, "unit": "TFLOP/s",
+           "frac": flop_ach / alu_peak, "traffic": traffic,
+           "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock"}
+    hbm = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
+           "frac": hbm_ach / hbm_peak, "traffic": traffic,
+           "peak_note": f"{src} STREAM copy"}
+    roof = dict(alu if alu["frac"] >= hbm["frac"] else hbm)
+    roof["other"] = hbm if roof["bound"] == "alu" else alu
+    return roof
+
+
 def cpu_oracle_rate(spec, phi0, g, steps: int = 1):
     """The FP64 oracle as it stands, on the host cores: `steps` full RK steps
     of the workload from phi0.  Returns (updates/s, seconds, threads)."""
@@ -329,23 +351,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     # ---- roofline of the dominant kernel (the fused stage kernel): its
     # average launch time over the timed region = solve time / stage launches
-    peaks, src = _peaks()
     per_launch_s = (ms / 1e3) / (stages * args.steps)
     bpn, fpn = algorithmic(spec)
-    hbm_ach = bpn * npts / per_launch_s / 1e9
-    flop_ach = fpn * npts / per_launch_s / 1e12
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes, TFLOP/s
-    hbm_peak = float(peaks["hbm_gbs"])
-    traffic = measured_traffic(spec["name"])
-    alu = {"bound": "alu", "achieved": flop_ach, "peak": alu_peak, "unit": "TFLOP/s",
-           "frac": flop_ach / alu_peak, "traffic": traffic,
-           "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock"}
-    hbm = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
-           "frac": hbm_ach / hbm_peak, "traffic": traffic,
-           "peak_note": f"{src} STREAM copy"}
-    roof = dict(alu if alu["frac"] >= hbm["frac"] else hbm)
-    roof["other"] = hbm if roof["bound"] == "alu" else alu
+    roof = roofline_of(fpn * npts, bpn * npts, per_launch_s, measured_traffic(spec["name"]))
 
     # ---- the oracle on this host's cores: a bounded sample of the workload
     cpu = None
@@ -504,6 +512,17 @@ def run_batched(args, rank: int, world: int, local_rank: int):
         return 0
     # one launch per stage, or one cooperative launch per solve
     launches = 1 if persistent else max(st["steps"] for st in stats) * specs[0]["rk"]
+    # roofline of the batched stage kernel (the only kernel of the solve):
+    # this rank's algorithmic work per solve over the solve time, averaged
+    # over its launches the same way
+    tot_f = tot_b = 0.0
+    for sp, st in zip(specs, stats):
+        bpn, fpn = algorithmic(sp)
+        nst = float(np.prod(sp["n"])) * st["stages"]
+        tot_f += fpn * nst
+        tot_b += bpn * nst
+    roof = roofline_of(tot_f / launches, tot_b / launches, (ms / 1e3) / args.steps / launches,
+                       None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -519,7 +538,7 @@ def run_batched(args, rank: int, world: int, local_rank: int):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo},
         "gpu_launches": launches * args.steps,
-        "roofline": None, "cpu_baseline": None, "clocks": clk.summary(),
+        "roofline": roof, "cpu_baseline": None, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
     return 0

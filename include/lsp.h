@@ -228,7 +228,10 @@ lsp_status lsp_hj_solve(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
  * instructions, pair = 2 the same with the marching axis' WENO5 terms
  * evaluated once per face (shared by the two nodes of the face; results
  * identical to pair = 1 bit for bit).
- *  lsp_set_tile(g, 0, 0, 0, 0, 0)   default (32 x 8, chunked for >= 2 waves, 3, 0)
+ *  lsp_set_tile(g, 0, 0, 0, 0, 0)   default: WENO5 16 x 16, 3 CTAs/SM, pair 2,
+ *                                   chunks for ~3 waves (even length); other
+ *                                   schemes 32 x 8, 3 CTAs/SM, chunks for ~2
+ *                                   waves
  *  lsp_set_tile(g, -1, 0, 0, 0, 0)  always use the generic kernel
  *  lsp_set_tile(g, tb, ta, ch, minb, pair) explicit; LSP_EINVAL unless
  *        tb*ta <= 256, the haloed tile fits 4 values per thread, the launch

@@ -269,7 +269,10 @@ template <int NDIM, int SCHEME, int DYN, typename R>
 __global__ void __launch_bounds__(256) adj_stage_a(AdjArgs<R> a)
 {
     constexpr int G = ghost_width(SCHEME);
-    double acc_h[4] = {0, 0, 0, 0}, acc_a[4] = {0, 0, 0, 0}, acc_dt = 0.0;
+    // per-thread partial sums in the field precision (a thread visits a few
+    // nodes), promoted to FP64 once for the block reduction: per-node FP64
+    // arithmetic would run on GB300's slow FP64 pipe
+    R acc_h[4] = {0, 0, 0, 0}, acc_a[4] = {0, 0, 0, 0}, acc_dt = R(0);
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < a.npts;
          idx += gridDim.x * blockDim.x) {
         int c[NDIM];
@@ -310,14 +313,14 @@ __global__ void __launch_bounds__(256) adj_stage_a(AdjArgs<R> a)
         }
         a.lam_v[idx] = lv;
         const R w = a.c_l * a.dt * lv;
-        acc_dt += (double)(a.c_l * lv) * (double)L;
+        acc_dt += (a.c_l * lv) * L;
         R hp[NDIM], hprm[4];
         ham_grad<DYN, NDIM>(x, pbar, a.prm, sth, cth, hp, hprm);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc_h[j] += (double)(w * -hprm[j]);
+        for (int j = 0; j < 4; ++j) acc_h[j] += w * -hprm[j];
 #pragma unroll
         for (int k = 0; k < NDIM; ++k) {
-            acc_a[k] += (double)(w * R(0.5) * (pp[k] - pm[k]));
+            acc_a[k] += w * R(0.5) * (pp[k] - pm[k]);
             R gm[7], gp[7];
             window_grad<SCHEME>(win[k] + 0, a.inv_dx[k], weno_floor12(a.inv_dx[k]), gm, gp);
             const R sp = w * (R(-0.5) * hp[k] + R(0.5) * a.alpha[k]);
@@ -351,7 +354,9 @@ __global__ void __launch_bounds__(256) adj_stage_a(AdjArgs<R> a)
     // block reductions of the accumulators, one FP64 atomic each per block
     __shared__ double red[9][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double vals[9] = {acc_h[0], acc_h[1], acc_h[2], acc_h[3], acc_a[0], acc_a[1], acc_a[2], acc_a[3], acc_dt};
+    const double vals[9] = {(double)acc_h[0], (double)acc_h[1], (double)acc_h[2], (double)acc_h[3],
+                            (double)acc_a[0], (double)acc_a[1], (double)acc_a[2], (double)acc_a[3],
+                            (double)acc_dt};
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         double v = vals[q];

@@ -128,21 +128,29 @@ double cfl_dt_host(const lsp_grid* g, double cfl, double t, double t_final)
 // Default tile: 32 x 8 threads over the two fastest axes, the march along
 // the third split into chunks so that at least ~2 waves of 2 CTAs per SM
 // are launched.
-lsp::Tile default_tile(const lsp_grid* g)
+// The tile used without lsp_set_tile / lsp_autotune: WENO5 runs the paired
+// shared-face kernel on 16 x 16 tiles, chunked so that the launch has about
+// three waves of 3 CTAs per SM, with an even chunk length (the pairs of
+// planes); the other schemes the scalar kernel on 32 x 8 tiles, about two
+// waves of 2 CTAs per SM.
+lsp::Tile default_tile(const lsp_grid* g, int scheme)
 {
     const int d = g->ndim;
+    const bool paired = scheme == LSP_WENO5;
     lsp::Tile t;
-    t.tb = 32;
-    t.ta = 8;
+    t.tb = paired ? 16 : 32;
+    t.ta = paired ? 16 : 8;
     t.minb = 3;
-    t.pair = 0;
+    t.pair = paired ? 2 : 0;
     const long long nplane = (long long)((g->n[d - 1] + t.tb - 1) / t.tb) *
                              ((g->n[d - 2] + t.ta - 1) / t.ta) * (d == 4 ? g->n[0] : 1);
-    long long nch = (2LL * 2 * 152 + nplane - 1) / nplane;
+    const long long want = paired ? 3LL * 3 * 152 : 2LL * 2 * 152;
+    long long nch = (want + nplane - 1) / nplane;
     const int nS = g->n[d - 3];
     if (nch > nS / 4) nch = nS / 4;
     if (nch < 1) nch = 1;
     t.ch = (int)((nS + nch - 1) / nch);
+    if (paired && (t.ch & 1)) t.ch += 1;
     return t;
 }
 
@@ -151,7 +159,7 @@ lsp::Tile tile_in_effect(const lsp_grid* g, const lsp_solve_opts* o)
 {
     lsp::Tile none{0, 0, 0, 0, 0};
     if (o->dtype != LSP_F32 || (g->ndim != 3 && g->ndim != 4) || g->tile_mode < 0) return none;
-    lsp::Tile t = g->tile_mode == 1 ? g->tile : default_tile(g);
+    lsp::Tile t = g->tile_mode == 1 ? g->tile : default_tile(g, o->scheme);
     return lsp::tile_valid(g->ndim, o->scheme, t, g->n) ? t : none;
 }
 

@@ -37,7 +37,9 @@ __device__ __forceinline__ F2 weno_phi2(F2 is0, F2 is1, F2 is2, F2 e, F2 A, F2 B
 {
     const F2 sc(__uint_as_float(0x7f000000u - (__float_as_uint(e.v.x) & 0x7f800000u)),
                 __uint_as_float(0x7f000000u - (__float_as_uint(e.v.y) & 0x7f800000u)));
-    const F2 q0 = (is0 + e) * sc, q1 = (is1 + e) * sc, q2 = (is2 + e) * sc;
+    // (is + e) sc as fma(is, sc, e sc): the same value (sc is a power of two)
+    const F2 esc = e * sc;
+    const F2 q0 = fma2(is0, sc, esc), q1 = fma2(is1, sc, esc), q2 = fma2(is2, sc, esc);
     const F2 Q0 = q0 * q0, Q1 = q1 * q1, Q2 = q2 * q2;
     const F2 Q12 = Q1 * Q2, Q01 = Q0 * Q1;
     const F2 P = fma2(F2(6.0f) * Q0, Q2, fma2(F2(3.0f), Q01, Q12));

@@ -255,8 +255,8 @@ def test_shared_faces_bitwise_equal_to_paired_planes(kind):
     """pair = 2 evaluates the marching axis' WENO5 corrections once per face
     and hands the left-biased one to the next plane; it performs the same
     operations on the same operands as pair = 1, so whole RK3 steps agree
-    bit for bit (ragged grids, odd and even chunk lengths, chunks of one
-    plane, periodic and extrapolated marching axes)."""
+    bit for bit (ragged grids, partial tiles, odd and even chunk lengths,
+    chunks of one plane, periodic and extrapolated axes)."""
     if kind == "air3d":
         spec = W.air3d(nx=[37, 29, 45])[0]
     elif kind == "car4d":
