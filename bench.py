@@ -50,10 +50,28 @@ def workload(name: str):
         spec, phi0, g = W.air3d(n=int(name[6:]))
     elif name.startswith("car4d_") and name[6:].isdigit():
         spec, phi0, g = W.car4d(n=int(name[6:]))
+    elif name.startswith("rockets_") and name[8:].isdigit():
+        spec, phi0, g = W.rockets(n=int(name[8:]))
+    elif name.startswith("double_integrator_") and name[18:].isdigit():
+        spec, phi0, g = W.double_integrator(n=int(name[18:]))
     elif name == "normal_speed_2d":
         spec, phi0, g = W.normal_speed_2d(101)
     else:
         raise SystemExit(f"unknown workload {name}")
+    return spec, phi0, g
+
+
+def workload_for(args):
+    """The workload of the command line with its dissipation / variational
+    options applied (the name records them)."""
+    spec, phi0, g = workload(args.workload)
+    if args.diss != "glf":
+        spec["diss"] = args.diss
+        spec["name"] += "_" + args.diss
+    if args.varform:
+        spec["varform"] = True
+        spec["tube"] = False  # the variational form stands in for the min with the target
+        spec["name"] += "_varform"
     return spec, phi0, g
 
 
@@ -75,7 +93,7 @@ COMBINE_FLOPS = 7
 
 def ham_flops(dyn: str, d: int) -> int:
     return {"air3d": 15, "car4d": 10, "normal_speed": 2 * d + 1, "translate": 2 * d - 1,
-            "quadratic": 2 * d}[dyn]
+            "quadratic": 2 * d, "rockets": 14, "double_integrator": 4}[dyn]
 
 
 def algorithmic(spec) -> tuple[float, float]:
@@ -211,7 +229,7 @@ def cpu_oracle_rate(spec, phi0, g, steps: int = 1):
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return 0
-    spec, phi0, g = workload(args.workload)
+    spec, phi0, g = workload_for(args)
     import numpy as np
     npts = int(np.prod(spec["n"]))
     for _ in range(args.warmup):
@@ -249,7 +267,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         BLD.build()
     if world > 1:
         torch.distributed.barrier()
-    spec, phi0, g = workload(args.workload)
+    spec, phi0, g = workload_for(args)
     npts = int(np.prod(spec["n"]))
     P = B.Problem(spec, use_graph=args.graph)
     tdt = P.torch_dtype
@@ -651,6 +669,83 @@ def run_adjoint(args, rank: int, world: int, local_rank: int):
     return 0
 
 
+def run_shapes(args, rank: int, world: int, local_rank: int):
+    """Implicit surfaces on the device (Sec. III-C, III-D): one benchmark step
+    builds a target on the air3d 201^3 grid -- a cylinder, a box and their
+    union -- i.e. two primitive kernels (4 B written per node each) and one
+    set operation (8 B read, 4 B written per node).  Metric: node values
+    produced per second; HBM roofline of the step's algorithmic bytes."""
+    import numpy as np
+    import torch
+
+    from paper_2411_03501_gb300 import binding as B
+    from paper_2411_03501_gb300 import build as BLD
+    from paper_2411_03501_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0 or not os.path.exists(BLD.LIB):
+        BLD.build()
+    spec = W.air3d(n=201)[0]
+    npts = int(np.prod(spec["n"]))
+    g = B.lsp_grid_create(3, spec["lo"], spec["hi"], spec["n"],
+                          ["periodic" if p else "extrapolate" for p in spec["periodic"]])
+    a = torch.empty(spec["n"], dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    out = torch.empty_like(a)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        B.lsp_shape_sphere(g, a, [0.0, 0.0, 0.0], 5.0, ignore=(2,))
+        B.lsp_shape_box(g, b, [2.0, -3.0, 0.0], [12.0, 3.0, 6.0], ignore=(2,))
+        B.lsp_shape_op("union", a, b, out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(local_rank, os.path.join(args.outdir, f"clocks_rank{rank}.csv"))
+    with clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t.item())
+    value = 3.0 * npts * args.steps * world / (ms / 1e3)
+    # the three kernels together: 4 + 4 + 12 algorithmic bytes per node
+    roof = roofline_of(0.0, 20.0 * npts, (ms / 1e3) / args.steps, None)
+    if rank != 0:
+        return 0
+    h_out = torch.empty(spec["n"], dtype=torch.float32).pin_memory()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        step()
+        h_out.copy_(out, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = 3.0 * npts * args.steps / (e2.elapsed_time(e3) / 1e3)
+    line = {
+        "metric": "implicit-surface node values/s", "value": value, "unit": "values/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "shapes_cylinder_box_union_201^3", "points": npts,
+                   "kernels_per_step": 3, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "fields of 32.5 MB, three per step (partly L2-resident); no flush"},
+        "e2e": {"value": e2e_value, "unit": "values/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": npts * 4},
+        "gpu_launches": 3 * args.steps, "roofline": roof, "cpu_baseline": None,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def adjoint_launches(nsteps: int, rk: int) -> int:
     """Kernels of one gradient evaluation: forward stages, the segment
     recomputation from sqrt(N) checkpoints, the per-step recomputation of the
@@ -672,7 +767,7 @@ def run_steps(args):
     from paper_2411_03501_gb300 import binding as B
     from paper_2411_03501_gb300 import build as BLD
     BLD.build()
-    spec, phi0, g = workload(args.workload)
+    spec, phi0, g = workload_for(args)
     P = B.Problem(spec)
     phi = torch.as_tensor(phi0).to("cuda", P.torch_dtype).contiguous()
     gd = torch.as_tensor(g).to("cuda", P.torch_dtype).contiguous() if g is not None else None
@@ -713,6 +808,10 @@ def main():
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--tile", default="", help="tb,ta,ch,minb: fixed tile instead of autotuning")
     ap.add_argument("--print-kernel-hash", action="store_true")
+    ap.add_argument("--diss", default="glf", choices=["glf", "llf", "lllf"],
+                    help="dissipation coefficients of the solve workloads")
+    ap.add_argument("--varform", type=int, default=0,
+                    help="1: the variational form of the tube PDE instead of the min with the target")
     ap.add_argument("--persistent", type=int, default=0,
                     help="batched workload: time the persistent launch (1) or the "
                          "stage-synchronous graph (0); the other is timed beside it")
@@ -739,6 +838,8 @@ def main():
             return run_batched(args, rank, world, local_rank)
         if args.workload == "adjoint":
             return run_adjoint(args, rank, world, local_rank)
+        if args.workload == "shapes":
+            return run_shapes(args, rank, world, local_rank)
         return run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:

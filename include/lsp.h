@@ -363,8 +363,8 @@ lsp_status lsp_loss_tube(const lsp_grid* grid, int dtype, const void* phi, const
  * the shape and which is negative inside; distances are measured in the
  * dimensions whose bit is clear in `ignore_mask` (bit k = dimension k), so
  * ignoring dimensions extrudes the shape along them (a sphere becomes a
- * cylinder).  Periodic axes are not wrapped.  Arithmetic in FP64, stored
- * in `dtype`; `out` is a device field of the grid's size.  Asynchronous.
+ * cylinder).  Periodic axes are not wrapped.  Arithmetic in `dtype`; `out`
+ * is a device field of the grid's size.  Asynchronous.
  *  lsp_shape_sphere     |x - center| - radius (signed distance)
  *  lsp_shape_box        signed distance to the box [lo, hi] (exact: the
  *                       Euclidean distance outside, minus the distance to

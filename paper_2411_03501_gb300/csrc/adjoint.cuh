@@ -247,7 +247,9 @@ struct AdjArgs {
     const R* target;   // read when tube
     const R* lam;      // dLoss/d out
     R* lam_v;          // out: dLoss/dv per node
-    R* contrib;        // out: NDIM * 7 coefficients per node (axis-major)
+    R* contrib;        // out: 7 NDIM coefficient fields, field q = 7 k + (o + 3)
+                       // (axis k, window offset o) at contrib + q * cstride
+    long long cstride; // elements between coefficient fields
     R* lam_u;          // ghost folds (atomics) here; pass B adds the rest
     R* lam_n;          // pass B: += c_n lam_v (may equal lam_u)
     R* lam_g;          // tube: += lam where the min took the target (nullable)
@@ -322,10 +324,10 @@ __global__ void __launch_bounds__(256) adj_stage_a(AdjArgs<R> a)
         for (int k = 0; k < NDIM; ++k) {
             acc_a[k] += w * R(0.5) * (pp[k] - pm[k]);
             R gm[7], gp[7];
-            window_grad<SCHEME>(win[k] + 0, a.inv_dx[k], weno_floor12(a.inv_dx[k]), gm, gp);
+            window_grad<SCHEME>(win[k], a.inv_dx[k], weno_floor12(a.inv_dx[k]), gm, gp);
             const R sp = w * (R(-0.5) * hp[k] + R(0.5) * a.alpha[k]);
             const R sm = w * (R(-0.5) * hp[k] - R(0.5) * a.alpha[k]);
-            R* out = a.contrib + ((long long)k * a.npts + idx) * 7;
+            R* out = a.contrib + (long long)(7 * k + 3) * a.cstride + idx;  // offset 0
             const int n = a.n[k], s = a.stride[k];
 #pragma unroll
             for (int o = -3; o <= 3; ++o) {
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(256) adj_stage_a(AdjArgs<R> a)
                     }
                     cf = R(0);
                 }
-                out[o + 3] = cf;
+                out[(long long)o * a.cstride] = cf;
             }
         }
     }
@@ -394,7 +396,7 @@ __global__ void __launch_bounds__(256) adj_stage_b(AdjArgs<R> a)
 #pragma unroll
         for (int k = 0; k < NDIM; ++k) {
             const int n = a.n[k], s = a.stride[k];
-            const R* ck = a.contrib + (long long)k * a.npts * 7;
+            const R* ck = a.contrib + (long long)(7 * k + 3) * a.cstride;  // offset 0
 #pragma unroll
             for (int o = -3; o <= 3; ++o) {
                 int i = c[k] - o;  // the node whose window offset o is this node
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(256) adj_stage_b(AdjArgs<R> a)
                     i = i < 0 ? i + n : i - n;
                 }
                 const long long node = (long long)idx + (long long)(i - c[k]) * s;
-                acc += ck[node * 7 + (o + 3)];
+                acc += ck[(long long)o * a.cstride + node];
             }
         }
         if (a.lam_n != a.lam_u && a.lam_n) a.lam_n[idx] += a.c_n * lv;

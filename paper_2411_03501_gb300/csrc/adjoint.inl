@@ -13,24 +13,45 @@ static inline int adj_blocks(long long npts)
     return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
+// Pass A: one wave of resident CTAs (occupancy x SMs, queried once per
+// instantiation), so that each thread visits many nodes and the per-thread
+// tail -- the promotion of its partial sums and the FP64 warp reduction --
+// is paid once per ~30 nodes instead of once per ~3.
+template <int NDIM, int SCHEME, int DYN>
+static cudaError_t launch_pass_a(const AdjArgs<LSP_REAL>& a, cudaStream_t s)
+{
+    static const int resident = [] {
+        int dev = 0, nsm = 152, per = 1;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per, adj_stage_a<NDIM, SCHEME, DYN, LSP_REAL>, 256, 0) != cudaSuccess || per < 1)
+            per = 1;
+        return nsm * per;
+    }();
+    long long b = (a.npts + 255) / 256;
+    const int nb = (int)(b < resident ? (b < 1 ? 1 : b) : resident);
+    adj_stage_a<NDIM, SCHEME, DYN, LSP_REAL><<<nb, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int NDIM, int SCHEME>
 static cudaError_t adj_dyn(int dyn, const AdjArgs<LSP_REAL>& a, cudaStream_t s)
 {
-    const int nb = adj_blocks(a.npts);
+    cudaError_t e;
     switch (dyn) {
-    case NORMAL_SPEED: adj_stage_a<NDIM, SCHEME, NORMAL_SPEED, LSP_REAL><<<nb, 256, 0, s>>>(a); break;
-    case TRANSLATE: adj_stage_a<NDIM, SCHEME, TRANSLATE, LSP_REAL><<<nb, 256, 0, s>>>(a); break;
+    case NORMAL_SPEED: e = launch_pass_a<NDIM, SCHEME, NORMAL_SPEED>(a, s); break;
+    case TRANSLATE: e = launch_pass_a<NDIM, SCHEME, TRANSLATE>(a, s); break;
     case AIR3D:
-        if constexpr (NDIM == 3) { adj_stage_a<3, SCHEME, AIR3D, LSP_REAL><<<nb, 256, 0, s>>>(a); break; }
+        if constexpr (NDIM == 3) { e = launch_pass_a<3, SCHEME, AIR3D>(a, s); break; }
         return cudaErrorInvalidValue;
     case CAR4D:
-        if constexpr (NDIM == 4) { adj_stage_a<4, SCHEME, CAR4D, LSP_REAL><<<nb, 256, 0, s>>>(a); break; }
+        if constexpr (NDIM == 4) { e = launch_pass_a<4, SCHEME, CAR4D>(a, s); break; }
         return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
-    cudaError_t e = cudaGetLastError();
     if (e) return e;
-    adj_stage_b<NDIM, LSP_REAL><<<nb, 256, 0, s>>>(a);
+    adj_stage_b<NDIM, LSP_REAL><<<adj_blocks(a.npts), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

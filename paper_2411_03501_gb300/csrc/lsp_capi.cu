@@ -1161,6 +1161,7 @@ lsp_status adj_stage(const lsp_grid* g, const lsp_solve_opts* o, void* ws, const
     a.lam = lam;
     a.lam_v = (R*)((char*)ws + Lo.off_lamv);
     a.contrib = (R*)((char*)ws + Lo.off_contrib);
+    a.cstride = (long long)(Lo.F / sizeof(R));
     a.lam_u = lam_u;
     a.lam_n = lam_n;
     a.lam_g = tube ? lam_g : nullptr;

@@ -3,49 +3,51 @@
 // targets and initial fields without a host round trip.
 //
 // One thread per node (grid-stride), coordinates lo + i * dx per axis as the
-// stage kernels use them; the arithmetic is FP64 and the result is stored in
-// the field's precision.  Primitives measure distance in the non-ignored
+// stage kernels use them, in the field's precision (FP64 arithmetic for FP32
+// fields would run on GB300's slow FP64 pipe).  Primitives measure distance in the non-ignored
 // dimensions only (ignoring dimensions turns a sphere into a cylinder, a box
 // into a slab); periodic axes are not wrapped.
 #include <cmath>
 
 #include "../../include/lsp.h"
 #include "launch.h"
+#include "stencil.cuh"
 
 namespace lsp {
 
-__device__ __forceinline__ double shape_value(const ShapeGeom& g, const ShapeArgs& s, const double* x)
+template <typename R>
+__device__ __forceinline__ R shape_value(const ShapeGeom& g, const ShapeArgs& s, const R* x)
 {
     if (s.kind == SHAPE_SPHERE) {  // |x - c| - r
-        double q = 0.0;
+        R q = R(0);
         for (int k = 0; k < g.ndim; ++k)
-            if (!((s.ignore >> k) & 1u)) q += (x[k] - s.c[k]) * (x[k] - s.c[k]);
-        return sqrt(q) - s.r;
+            if (!((s.ignore >> k) & 1u)) q += (x[k] - R(s.c[k])) * (x[k] - R(s.c[k]));
+        return rsqrt_(q) - R(s.r);
     }
     if (s.kind == SHAPE_BOX) {  // exact signed distance to [c, d]
-        double out2 = 0.0, in = -INFINITY;
+        R out2 = R(0), in = R(-INFINITY);
         for (int k = 0; k < g.ndim; ++k) {
             if ((s.ignore >> k) & 1u) continue;
-            const double e = fmax(s.c[k] - x[k], x[k] - s.d[k]);  // > 0 outside this slab
-            if (e > 0.0) out2 += e * e;
-            in = fmax(in, e);
+            const R e = rmax(R(s.c[k]) - x[k], x[k] - R(s.d[k]));  // > 0 outside this slab
+            if (e > R(0)) out2 += e * e;
+            in = rmax(in, e);
         }
-        return out2 > 0.0 ? sqrt(out2) : in;
+        return out2 > R(0) ? rsqrt_(out2) : in;
     }
     if (s.kind == SHAPE_QUADRIC) {  // sum_k w_k (x_k - c_k)^2 - offset
-        double q = 0.0;
+        R q = R(0);
         for (int k = 0; k < g.ndim; ++k)
-            if (!((s.ignore >> k) & 1u)) q += s.d[k] * (x[k] - s.c[k]) * (x[k] - s.c[k]);
-        return q - s.r;
+            if (!((s.ignore >> k) & 1u)) q += R(s.d[k]) * (x[k] - R(s.c[k])) * (x[k] - R(s.c[k]));
+        return q - R(s.r);
     }
     // half space {n . (x - p) <= 0}: signed distance n . (x - p) / |n|
-    double q = 0.0, nn = 0.0;
+    R q = R(0), nn = R(0);
     for (int k = 0; k < g.ndim; ++k)
         if (!((s.ignore >> k) & 1u)) {
-            q += s.d[k] * (x[k] - s.c[k]);
-            nn += s.d[k] * s.d[k];
+            q += R(s.d[k]) * (x[k] - R(s.c[k]));
+            nn += R(s.d[k]) * R(s.d[k]);
         }
-    return q / sqrt(nn);
+    return q / rsqrt_(nn);
 }
 
 template <typename R>
@@ -53,13 +55,13 @@ __global__ void __launch_bounds__(256) shape_kernel(ShapeGeom g, ShapeArgs s, R*
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.npts;
          i += (long long)gridDim.x * blockDim.x) {
-        double x[LSP_MAXD];
+        R x[LSP_MAXD];
         long long r = i;
         for (int k = g.ndim - 1; k >= 0; --k) {
-            x[k] = g.lo[k] + double(r % g.n[k]) * g.h[k];
+            x[k] = R(g.lo[k]) + R(r % g.n[k]) * R(g.h[k]);
             r /= g.n[k];
         }
-        out[i] = R(shape_value(g, s, x));
+        out[i] = shape_value<R>(g, s, x);
     }
 }
 

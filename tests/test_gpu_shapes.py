@@ -1,5 +1,6 @@
 """Implicit surfaces on the device (through the C ABI) against the oracle's
-definitions, node by node, in FP64 and FP32, on ragged 2-D to 4-D grids."""
+definitions, node by node, in FP64 and FP32 arithmetic, on ragged 2-D to 4-D
+grids; set operations bit for bit."""
 import numpy as np
 import pytest
 import torch
@@ -25,13 +26,16 @@ def _grid(spec):
     return g
 
 
-def _check(got, want, dtype):
+def _check(got, want, dtype, scale):
+    """scale: the largest magnitude entering the primitive's arithmetic (the
+    coordinates, centre and radius; the weighted squares of a quadric); FP32
+    arithmetic is held to 32 units of 2^-24 of it, FP64 to 1e-12."""
     got = got.double().cpu().numpy()
     if dtype == torch.float64:
-        np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * max(1.0, np.abs(want).max()))
-    else:  # FP64 arithmetic (to ~1e-16 of the oracle's), one rounding to FP32
-        scale = max(1.0, np.abs(want).max())
-        assert np.all(np.abs(got - want) <= 2.0 ** -24 * np.abs(want) + 1e-13 * scale)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * scale)
+    else:
+        err = np.abs(got - want).max()
+        assert err <= 32 * 2.0 ** -24 * scale, (err, scale)
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
@@ -41,21 +45,23 @@ def test_primitives_match_oracle(ndim, dtype):
     g = _grid(spec)
     out = torch.empty(spec["n"], dtype=dtype, device="cuda")
     c = [0.3, -0.4, 1.0, 0.5][:ndim]
+    X = max(max(abs(v) for v in spec["lo"]), max(abs(v) for v in spec["hi"]))
+    lin = np.sqrt(ndim) * (X + 1.0) + 2.0  # distances, coordinates, centre, radius
     B.lsp_shape_sphere(g, out, c, 1.7)
-    _check(out, S.sphere(spec, c, 1.7), dtype)
+    _check(out, S.sphere(spec, c, 1.7), dtype, lin)
     B.lsp_shape_sphere(g, out, c, 1.2, ignore=(ndim - 1,))
-    _check(out, S.sphere(spec, c, 1.2, ignore=(ndim - 1,)), dtype)
+    _check(out, S.sphere(spec, c, 1.2, ignore=(ndim - 1,)), dtype, lin)
     lo, hi = [-1.0, -0.5, 0.5, 0.2][:ndim], [1.5, 0.8, 3.0, 1.1][:ndim]
     B.lsp_shape_box(g, out, lo, hi)
-    _check(out, S.box(spec, lo, hi), dtype)
+    _check(out, S.box(spec, lo, hi), dtype, lin)
     B.lsp_shape_box(g, out, lo, hi, ignore=(0,))
-    _check(out, S.box(spec, lo, hi, ignore=(0,)), dtype)
+    _check(out, S.box(spec, lo, hi, ignore=(0,)), dtype, lin)
     w = [1.0, 4.0, 9.0, 2.0][:ndim]
     B.lsp_shape_quadric(g, out, c, w, 2.5)
-    _check(out, S.quadric(spec, c, w, 2.5), dtype)
+    _check(out, S.quadric(spec, c, w, 2.5), dtype, sum(w) * (X + 1.0) ** 2 + 2.5)
     nrm = [1.0, -2.0, 0.5, 0.3][:ndim]
     B.lsp_shape_halfspace(g, out, nrm, c)
-    _check(out, S.halfspace(spec, nrm, c), dtype)
+    _check(out, S.halfspace(spec, nrm, c), dtype, 4.0 * lin)
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
