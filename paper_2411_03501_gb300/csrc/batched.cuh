@@ -6,6 +6,7 @@
 #include "../../include/lsp.h"
 #include "batched.h"
 #include "launch.h"
+#include "stage_pair.cuh"
 #include "stage_tiled.cuh"
 
 namespace lsp {
@@ -39,6 +40,30 @@ __device__ __forceinline__ void batch_stage_args(const BatchProblem& P, int step
     sa.target = P.target;
 }
 
+// The body of one tile of a 3-D / 4-D problem: the paired shared-face body
+// for the global-LF WENO5 stage (as single-problem solves run it by
+// default), the scalar body otherwise.
+template <int NDIM, int SCHEME, int DYN, bool COH, bool LOCAL>
+__device__ __forceinline__ void batch_body(const StageArgs<float>& sa, int bx, int by, int chunk,
+                                           int outer, int ch, float* tile, int tx, int ty)
+{
+    if constexpr (SCHEME == WENO5 && !LOCAL)
+        tiled_pair_body<NDIM, DYN, true, COH>(sa, kBatchTB, kBatchTA, bx, by, chunk, outer, ch,
+                                              tile, tx, ty);
+    else
+        tiled_stage_body<NDIM, SCHEME, DYN, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by,
+                                                               chunk, outer, ch, tile, tx, ty);
+}
+
+// Shared tile of a batched CTA: two double-buffered planes, four for the
+// paired body.
+template <int SCHEME, bool LOCAL>
+__host__ __device__ constexpr int batch_tile_floats()
+{
+    return ((SCHEME == WENO5 && !LOCAL) ? 4 : 2) * (kBatchTA + 2 * ghost_width(SCHEME)) *
+           (kBatchTB + 2 * ghost_width(SCHEME));
+}
+
 template <int SCHEME, bool COH, bool LOCAL>
 __device__ __forceinline__ void batch_tile(const BatchProblem& P, const StageArgs<float>& sa,
                                            int local, float* tile)
@@ -56,28 +81,28 @@ __device__ __forceinline__ void batch_tile(const BatchProblem& P, const StageArg
         tiled_stage_body<2, SCHEME, TRANSLATE, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by, 0, 0, 1, tile, tx, ty);
         break;
     case 3 * 8 + NORMAL_SPEED:
-        tiled_stage_body<3, SCHEME, NORMAL_SPEED, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by, chunk, 0, P.ch, tile, tx, ty);
+        batch_body<3, SCHEME, NORMAL_SPEED, COH, LOCAL>(sa, bx, by, chunk, 0, P.ch, tile, tx, ty);
         break;
     case 3 * 8 + TRANSLATE:
-        tiled_stage_body<3, SCHEME, TRANSLATE, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by, chunk, 0, P.ch, tile, tx, ty);
+        batch_body<3, SCHEME, TRANSLATE, COH, LOCAL>(sa, bx, by, chunk, 0, P.ch, tile, tx, ty);
         break;
     case 3 * 8 + AIR3D:
-        tiled_stage_body<3, SCHEME, AIR3D, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by, chunk, 0, P.ch, tile, tx, ty);
+        batch_body<3, SCHEME, AIR3D, COH, LOCAL>(sa, bx, by, chunk, 0, P.ch, tile, tx, ty);
         break;
     case 3 * 8 + ROCKETS:
-        tiled_stage_body<3, SCHEME, ROCKETS, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by, chunk, 0, P.ch, tile, tx, ty);
+        batch_body<3, SCHEME, ROCKETS, COH, LOCAL>(sa, bx, by, chunk, 0, P.ch, tile, tx, ty);
         break;
     case 2 * 8 + DOUBLE_INT:
         tiled_stage_body<2, SCHEME, DOUBLE_INT, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by, 0, 0, 1, tile, tx, ty);
         break;
     case 4 * 8 + NORMAL_SPEED:
-        tiled_stage_body<4, SCHEME, NORMAL_SPEED, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by, chunk, outer, P.ch, tile, tx, ty);
+        batch_body<4, SCHEME, NORMAL_SPEED, COH, LOCAL>(sa, bx, by, chunk, outer, P.ch, tile, tx, ty);
         break;
     case 4 * 8 + TRANSLATE:
-        tiled_stage_body<4, SCHEME, TRANSLATE, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by, chunk, outer, P.ch, tile, tx, ty);
+        batch_body<4, SCHEME, TRANSLATE, COH, LOCAL>(sa, bx, by, chunk, outer, P.ch, tile, tx, ty);
         break;
     case 4 * 8 + CAR4D:
-        tiled_stage_body<4, SCHEME, CAR4D, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by, chunk, outer, P.ch, tile, tx, ty);
+        batch_body<4, SCHEME, CAR4D, COH, LOCAL>(sa, bx, by, chunk, outer, P.ch, tile, tx, ty);
         break;
     default:
         break;  // rejected on the host
@@ -93,7 +118,7 @@ __global__ void __launch_bounds__(kBatchTB * kBatchTA, 3)
 {
     constexpr int G = ghost_width(SCHEME);
     __shared__ StageArgs<float> sa;
-    __shared__ float tile[2 * (kBatchTA + 2 * G) * (kBatchTB + 2 * G)];
+    __shared__ float tile[batch_tile_floats<SCHEME, LOCAL>()];
     const int p = block_prob[blockIdx.x];
     const BatchProblem& P = probs[p];
     const int tid = threadIdx.y * kBatchTB + threadIdx.x;
@@ -127,7 +152,7 @@ __global__ void __launch_bounds__(kBatchTB * kBatchTA, 3)
 {
     constexpr int G = ghost_width(SCHEME);
     __shared__ StageArgs<float> sa;
-    __shared__ float tile[2 * (kBatchTA + 2 * G) * (kBatchTB + 2 * G)];
+    __shared__ float tile[batch_tile_floats<SCHEME, LOCAL>()];
     __shared__ int s_p, s_local, s_stop;
     const int tid = threadIdx.y * kBatchTB + threadIdx.x;
     const long long total = segs[nseg].item_start;

@@ -18,7 +18,7 @@ struct BatchProblem {
     int block_start, nblocks;   // this problem's CTAs in the launch
 };
 
-constexpr int kBatchTB = 32, kBatchTA = 8;
+constexpr int kBatchTB = 16, kBatchTA = 16;
 
 // Persistent batched launch: work items (step k, stage s, tile b) are handed
 // out in this order by one counter; the steps split into segments with a

@@ -1569,7 +1569,7 @@ lsp_status lsp_shape_op(int op, int dtype, const void* a, const void* b, void* o
 {
     if (op < LSP_SHAPE_UNION || op > LSP_SHAPE_DIFFERENCE) return fail(LSP_EINVAL, "bad op");
     if (dtype != LSP_F32 && dtype != LSP_F64) return fail(LSP_EINVAL, "bad dtype");
-    if (n < 0) return fail(LSP_EINVAL, "n must be >= 0");
+    if (n < 0 || n >= (1LL << 31)) return fail(LSP_EINVAL, "n must be in [0, 2^31)");
     if (n > 0 && (!a || !out || (op != LSP_SHAPE_COMPLEMENT && !b)))
         return fail(LSP_EINVAL, "NULL field");
     cudaError_t e = lsp::launch_shape_op(op, dtype, a, b, out, (long long)n, (cudaStream_t)stream);

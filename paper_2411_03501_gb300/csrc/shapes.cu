@@ -53,13 +53,16 @@ __device__ __forceinline__ R shape_value(const ShapeGeom& g, const ShapeArgs& s,
 template <typename R>
 __global__ void __launch_bounds__(256) shape_kernel(ShapeGeom g, ShapeArgs s, R* out)
 {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.npts;
-         i += (long long)gridDim.x * blockDim.x) {
+    // 32-bit index arithmetic (the host checks npts < 2^31): 64-bit division
+    // per node would dominate these memory-bound kernels
+    const unsigned npts = (unsigned)g.npts;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += gridDim.x * blockDim.x) {
         R x[LSP_MAXD];
-        long long r = i;
+        unsigned r = i;
         for (int k = g.ndim - 1; k >= 0; --k) {
-            x[k] = R(g.lo[k]) + R(r % g.n[k]) * R(g.h[k]);
-            r /= g.n[k];
+            const unsigned nk = (unsigned)g.n[k], q = r / nk;
+            x[k] = R(g.lo[k]) + R(r - q * nk) * R(g.h[k]);
+            r = q;
         }
         out[i] = shape_value<R>(g, s, x);
     }
@@ -71,8 +74,8 @@ template <typename R>
 __global__ void __launch_bounds__(256) shape_op_kernel(int op, const R* a, const R* b, R* out,
                                                        long long n)
 {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < (unsigned)n;
+         i += gridDim.x * blockDim.x) {
         const R u = a[i];
         R v;
         switch (op) {

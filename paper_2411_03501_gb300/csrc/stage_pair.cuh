@@ -13,6 +13,15 @@
 
 namespace lsp {
 
+// phi^n may be written by the same launch when COH (persistent batched
+// solve): an L2 load then, a plain one otherwise.
+template <bool COH>
+__device__ __forceinline__ float ld_phin(const float* p)
+{
+    if constexpr (COH) return __ldcg(p);
+    else return *p;
+}
+
 template <int DYN, int NDIM>
 __device__ __forceinline__ F2 hamiltonian_pair(const F2* x, const F2* p, const float* prm, float s,
                                                float c)
@@ -30,7 +39,7 @@ __device__ __forceinline__ F2 hamiltonian_pair(const F2* x, const F2* p, const f
     } else if constexpr (DYN == AIR3D) {
         const float ve = prm[0], vp = prm[1], um = prm[2], dm = prm[3];
         const F2 sw = p[0] * x[1] - p[1] * x[0] - p[2];
-        const F2 v = p[0] * F2(-ve + vp * c) + p[1] * F2(vp * s) + F2(um) * abs2(sw) -
+        const F2 v = p[0] * F2(fmaf(vp, c, -ve)) + p[1] * F2(vp * s) + F2(um) * abs2(sw) -
                      F2(dm) * abs2(p[2]);
         return -v;
     } else if constexpr (DYN == CAR4D) {
@@ -57,7 +66,7 @@ __device__ __forceinline__ F2 hamiltonian_pair(const F2* x, const F2* p, const f
 // (weno5_face2): one face evaluation per node instead of two one-sided ones,
 // the left-biased correction of the next plane carried in a register.  The
 // results are bit-identical to FACES = false.
-template <int NDIM, int DYN, bool FACES = false>
+template <int NDIM, int DYN, bool FACES = false, bool COH = false>
 __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int TB, int TA, int bx,
                                                 int by, int chunk, int outer, int ch, float* tile,
                                                 int tx, int ty)
@@ -88,9 +97,9 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
     const float fl_b = weno_floor12(a.inv_dx[AB]);
 
     F2 x[NDIM];
-    if constexpr (NDIM == 4) x[0] = F2(a.lo[0] + float(outer) * a.h[0]);
-    x[AA] = F2(a.lo[AA] + float(ia) * a.h[AA]);
-    x[AB] = F2(a.lo[AB] + float(ib) * a.h[AB]);
+    if constexpr (NDIM == 4) x[0] = F2(fmaf(float(outer), a.h[0], a.lo[0]));
+    x[AA] = F2(fmaf(float(ia), a.h[AA], a.lo[AA]));
+    x[AB] = F2(fmaf(float(ib), a.h[AB], a.lo[AB]));
     float sth = 0.f, cth = 1.f;
     if constexpr (DYN == AIR3D || DYN == CAR4D || DYN == ROCKETS) sincosf(x[2].x(), &sth, &cth);
 
@@ -98,7 +107,7 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
     const float* col = a.phi_s + base_outer + ia_c * sA + ib_c;
     float w[2 * G + 2];
 #pragma unroll
-    for (int o = -G; o < G; ++o) w[o + G] = line_value(col, s_begin + o, nS, sS, a.periodic[AS]);
+    for (int o = -G; o < G; ++o) w[o + G] = line_value<float, COH>(col, s_begin + o, nS, sS, a.periodic[AS]);
 
     constexpr int MAXE = 4;
     int e_off[MAXE];
@@ -122,7 +131,7 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
         if (inner) {
 #pragma unroll
             for (int k = 0; k < MAXE; ++k)
-                if (k < nvalid) pf[k] = __ldg(plane + e_off[k]);
+                if (k < nvalid) pf[k] = ld_in<COH>(plane + e_off[k]);
             return;
         }
 #pragma unroll
@@ -130,14 +139,14 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
             const unsigned kind = (kinds >> (2 * k)) & 3u;
             float v = 0.f;
             if (kind == 0u) {
-                v = __ldg(plane + e_off[k]);
+                v = ld_in<COH>(plane + e_off[k]);
             } else if (kind == 1u) {
                 const int e = tid + k * nthr;
-                v = line_value(plane + e_off[k] * sA, b0 - G + (e - (e / W) * W), nB, 1,
+                v = line_value<float, COH>(plane + e_off[k] * sA, b0 - G + (e - (e / W) * W), nB, 1,
                                a.periodic[AB]);
             } else if (kind == 2u) {
                 const int e = tid + k * nthr;
-                v = line_value(plane + e_off[k], a0 - G + e / W, nA, sA, a.periodic[AA]);
+                v = line_value<float, COH>(plane + e_off[k], a0 - G + e / W, nA, sA, a.periodic[AA]);
             }
             pf[k] = v;
         }
@@ -147,8 +156,8 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
     fetch(min(s_begin + 1, nS - 1), pfB);
     // value j >= 0 of this thread's column along S (plain load inside the grid)
     auto col_value = [&](int j) -> float {
-        if (j < nS) return __ldg(col + j * sS);
-        return line_value(col, j, nS, sS, a.periodic[AS]);
+        if (j < nS) return ld_in<COH>(col + j * sS);
+        return line_value<float, COH>(col, j, nS, sS, a.periodic[AS]);
     };
     float wnA = col_value(s_begin + G);
     float wnB = col_value(s_begin + G + 1);
@@ -221,25 +230,26 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
                 if (outer >= G && outer + G < a.n[0]) {  // block-uniform: no ghost cells
 #pragma unroll
                     for (int o = -G; o <= G; ++o)
-                        u[o + G] = F2(__ldg(c0 + (outer + o) * a.stride[0]),
-                                      __ldg(c1 + (outer + o) * a.stride[0]));
+                        u[o + G] = F2(ld_in<COH>(c0 + (outer + o) * a.stride[0]),
+                                      ld_in<COH>(c1 + (outer + o) * a.stride[0]));
                 } else {
 #pragma unroll
                     for (int o = -G; o <= G; ++o)
-                        u[o + G] = F2(line_value(c0, outer + o, a.n[0], a.stride[0], a.periodic[0]),
-                                      line_value(c1, outer + o, a.n[0], a.stride[0],
+                        u[o + G] = F2(line_value<float, COH>(c0, outer + o, a.n[0], a.stride[0], a.periodic[0]),
+                                      line_value<float, COH>(c1, outer + o, a.n[0], a.stride[0],
                                                  a.periodic[0]));
                 }
                 deriv_weno5_jp2(u, a.inv_dx[0], weno_floor12(a.inv_dx[0]), pm, pp);
                 pbar[0] = F2(0.5f) * (pp + pm);
                 diss = fma2(F2(0.5f * alpha[0]), pp - pm, diss);
             }
-            x[AS] = F2(a.lo[AS] + float(s) * a.h[AS], a.lo[AS] + float(s + 1) * a.h[AS]);
+            x[AS] = F2(fmaf(float(s), a.h[AS], a.lo[AS]), fmaf(float(s + 1), a.h[AS], a.lo[AS]));
             const F2 Hv = hamiltonian_pair<DYN, NDIM>(x, pbar, a.prm, sth, cth);
             const F2 L = diss - Hv;
             const int idx = base_outer + s * sS + ia * sA + ib;
             F2 v = fma2(cs, center, cl * L);
-            if (a.phi_n) v = fma2(cn, F2(a.phi_n[idx], second ? a.phi_n[idx + sS] : 0.f), v);
+            if (a.phi_n)
+                v = fma2(cn, F2(ld_phin<COH>(a.phi_n + idx), second ? ld_phin<COH>(a.phi_n + idx + sS) : 0.f), v);
             if (a.tube) v = min2(v, F2(__ldg(a.target + idx), second ? __ldg(a.target + idx + sS) : 0.f));
             nonfinite |= !isfinite(v.x()) || (second && !isfinite(v.y()));
             a.out[idx] = v.x();

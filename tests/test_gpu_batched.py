@@ -24,9 +24,9 @@ def _mixed(scale=0.15, count=12, seed=20241105):
 def test_batched_equals_single_problem_solves(use_graph):
     """Every problem of a mixed 2-D / 3-D batch ends where its own
     single-problem solve ends: bit for bit for the 3-D problems run with the
-    scalar tiled body (the one the batched kernel inlines; same arithmetic per
-    node), to FP32 rounding for the 2-D ones (the single-problem path runs
-    the generic kernel there)."""
+    paired shared-face body (the one the batched kernel inlines for WENO5;
+    same arithmetic per node), to FP32 rounding for the 2-D ones (the
+    single-problem path runs the generic kernel there)."""
     specs, phis, gs = _mixed()
     Bt = B.Batch(specs, use_graph=use_graph, check_finite=True)
     xs = [to_dev(p, "f32") for p in phis]
@@ -36,7 +36,7 @@ def test_batched_equals_single_problem_solves(use_graph):
     for i, sp in enumerate(specs):
         P = B.Problem(sp)
         if sp["ndim"] == 3:
-            P.set_tile(32, 8, 32, 3, 0)  # the scalar tiled body the batched kernel runs
+            P.set_tile(16, 16, 32, 3, 2)  # the paired body the batched kernel runs for WENO5
         y = to_dev(phis[i], "f32")
         st = P.solve(y, gts[i])
         torch.cuda.synchronize()
