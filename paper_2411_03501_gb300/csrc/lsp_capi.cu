@@ -709,7 +709,25 @@ lsp_status lsp_autotune(lsp_grid* g, const lsp_solve_opts* o, const void* phi, v
     }
     if (!g->alpha_state) return fail(LSP_EUNSUPPORTED, "autotune needs state-only LF bounds");
     const int d = g->ndim;
-    const int shapes[][2] = {{32, 8}, {32, 4}, {16, 8}, {16, 16}, {64, 4}, {32, 6}, {48, 4}};
+    // fixed shapes, then two fitted to the grid: about 32 (16) nodes of the
+    // fastest axis and as many rows as 256 threads allow, each rounded up so
+    // that the tiles divide the two axes evenly (81 nodes: 27 x 9, 14 x 17),
+    // which leaves fewer idle threads in the last tile of a row or column
+    int shapes[9][2] = {{32, 8}, {32, 4}, {16, 8}, {16, 16}, {64, 4}, {32, 6}, {48, 4}};
+    int nshapes = 7;
+    for (const int wmax : {32, 16}) {
+        const int nB = g->n[d - 1], nA = g->n[d - 2];
+        const int tb = (nB + (nB + wmax - 1) / wmax - 1) / ((nB + wmax - 1) / wmax);
+        const int hmax = 256 / tb;
+        const int ta = (nA + (nA + hmax - 1) / hmax - 1) / ((nA + hmax - 1) / hmax);
+        bool dup = false;
+        for (int i = 0; i < nshapes; ++i) dup |= shapes[i][0] == tb && shapes[i][1] == ta;
+        if (!dup) {
+            shapes[nshapes][0] = tb;
+            shapes[nshapes][1] = ta;
+            ++nshapes;
+        }
+    }
     const int splits[] = {1, 2, 3, 4, 6, 8, 12};
     lsp::Ctl* ctl = (lsp::Ctl*)ws;
     float* w1 = (float*)((char*)ws + lsp::kCtlBytes);
@@ -721,7 +739,8 @@ lsp_status lsp_autotune(lsp_grid* g, const lsp_solve_opts* o, const void* phi, v
     float best_ms = 1e30f;
     lsp::Tile best{0, 0, 0, 0, 0};
     const double dt = cfl_dt_host(g, o->cfl, 0.0, INFINITY);
-    for (const auto& sh : shapes) {
+    for (int si = 0; si < nshapes; ++si) {
+        const int* sh = shapes[si];
         for (int cand = 0; cand < 63; ++cand) {
             const int sp = splits[cand % 7];
             const int minb = 2 + (cand / 7) % 3;

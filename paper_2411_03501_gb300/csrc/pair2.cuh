@@ -48,22 +48,30 @@ __device__ __forceinline__ F2 weno_phi2(F2 is0, F2 is1, F2 is2, F2 e, F2 A, F2 B
     return fma2(w0 * F2(1.0f / 3.0f), A, (w2 - F2(0.5f)) * (B * F2(1.0f / 6.0f)));
 }
 
-// deriv_weno5_jp for two nodes: u[o] holds the window values at offset o-3
-// of both nodes.
-__device__ __forceinline__ void deriv_weno5_jp2(const F2* u, float inv_dx, float floor12, F2& pm,
-                                                F2& pp)
+// The parts of deriv_weno5_jp for two nodes: u[o] holds the window values
+// at offset o-3 of both nodes; p- = (cen - phim) / dx, p+ = (cen + phip) / dx
+// (the caller combines them, see lf_axis2).
+__device__ __forceinline__ void weno5_jp2(const F2* u, float floor12, F2& cen, F2& phim, F2& phip)
 {
     const F2 dm3 = u[1] - u[0], dm2 = u[2] - u[1], dm1 = u[3] - u[2];
     const F2 d0 = u[4] - u[3], d1 = u[5] - u[4], d2 = u[6] - u[5];
     const F2 Sm2 = dm2 - dm3, Sm1 = dm1 - dm2, S0 = d0 - dm1, S1 = d1 - d0, S2 = d2 - d1;
-    const F2 cen = (fma2(F2(7.0f), dm1 + d0, -(dm2 + d1))) * F2(1.0f / 12.0f);
-    const F2 m4 = max2(max2(dm2 * dm2, dm1 * dm1), max2(d0 * d0, d1 * d1));
-    const F2 eL = fma2(F2(1.2e-5f), max2(m4, dm3 * dm3), F2(floor12));
-    const F2 eR = fma2(F2(1.2e-5f), max2(m4, d2 * d2), F2(floor12));
+    // (7 (dm1 + d0) - (dm2 + d1)) / 12 from its negation: fma(-7, x, y) is
+    // exactly -fma(7, x, -y), and the product of two negated factors rounds
+    // like the plain one (no paired negation is issued)
+    cen = fma2(F2(-7.0f), dm1 + d0, dm2 + d1) * F2(-1.0f / 12.0f);
+    // max_k d_k^2 as (max_k |d_k|)^2: squaring rounds monotonically on
+    // [0, inf), so the two are the same number; the max runs on the ALU
+    const F2 m4 = max2(max2(abs2(dm2), abs2(dm1)), max2(abs2(d0), abs2(d1)));
+    const F2 mL = max2(m4, abs2(dm3)), mR = max2(m4, abs2(d2));
+    const F2 eL = fma2(F2(1.2e-5f), mL * mL, F2(floor12));
+    const F2 eR = fma2(F2(1.2e-5f), mR * mR, F2(floor12));
     const F2 g1 = Sm2 - Sm1, g2 = Sm1 - S0, g3 = S0 - S1, g4 = S1 - S2;
     const F2 e1 = g1 * g1, e2 = g2 * g2, e3 = g3 * g3, e4 = g4 * g4;
-    const F2 f0m = fma2(F2(-3.0f), Sm1, Sm2), f1m = Sm1 + S0, f2m = fma2(F2(3.0f), S0, -S1);
-    const F2 f0p = fma2(F2(-3.0f), S1, S2), f1p = S1 + S0, f2p = fma2(F2(3.0f), S0, -Sm1);
+    // f2m and f2p enter only squared: their negations -(3 S0 - S1) and
+    // -(3 S0 - Sm1) are one FMA each and give the same squares
+    const F2 f0m = fma2(F2(-3.0f), Sm1, Sm2), f1m = Sm1 + S0, f2m = fma2(F2(-3.0f), S0, S1);
+    const F2 f0p = fma2(F2(-3.0f), S1, S2), f1p = S1 + S0, f2p = fma2(F2(-3.0f), S0, Sm1);
     const F2 three(3.0f), thirteen(13.0f);
     const F2 is0m = fma2(thirteen, e1, three * f0m * f0m);
     const F2 is1m = fma2(thirteen, e2, three * f1m * f1m);
@@ -74,8 +82,21 @@ __device__ __forceinline__ void deriv_weno5_jp2(const F2* u, float inv_dx, float
     const F2 two(2.0f);
     const F2 Tm1 = fma2(-two, Sm1, Sm2 + S0), T0 = fma2(-two, S0, Sm1 + S1);
     const F2 T1 = fma2(-two, S1, S0 + S2);
-    pm = (cen - weno_phi2(is0m, is1m, is2m, eL, Tm1, T0)) * F2(inv_dx);
-    pp = (cen + weno_phi2(is0p, is1p, is2p, eR, T1, T0)) * F2(inv_dx);
+    phim = weno_phi2(is0m, is1m, is2m, eL, Tm1, T0);
+    phip = weno_phi2(is0p, is1p, is2p, eR, T1, T0);
+}
+
+// One axis' share of the LF rate (Sec. IV-D) from the parts of its WENO5
+// derivatives: the central costate (p+ + p-)/2 = (cen + (phip - phim)/2)/dx
+// and the dissipation alpha (p+ - p-)/2 = alpha/(2 dx) (phip + phim), added
+// to diss; hax = alpha/(2 dx).  The centred term cancels from the
+// difference instead of being subtracted after rounding, and the pair costs
+// five paired instructions instead of eight.
+__device__ __forceinline__ void lf_axis2(F2 cen, F2 phim, F2 phip, F2 sx, F2 hax, F2& pbar,
+                                         F2& diss)
+{
+    pbar = fma2(F2(0.5f), phip - phim, cen) * sx;
+    diss = fma2(hax, phip + phim, diss);
 }
 
 // The two WENO5 corrections that share the face between nodes j and j+1,
@@ -85,7 +106,7 @@ __device__ __forceinline__ void deriv_weno5_jp2(const F2* u, float inv_dx, float
 // smoothness indicators are the same three numbers in reversed order and
 // their regulariser is the same; everything up to the squared scaled
 // indicators is computed once.  Each result is bit-identical to the
-// corresponding weno_phi2 call of deriv_weno5_jp2 (the same operations on the
+// corresponding weno_phi2 call of weno5_jp2 (the same operations on the
 // same operands: negated FMAs round symmetrically, products commute, and the
 // scaling by an exact power of two commutes with rounding, so
 // fma(is, sc, e*sc) == (is + e) * sc).  cen receives the centred term of
@@ -95,14 +116,14 @@ __device__ __forceinline__ void weno5_face2(const F2* v, float floor12, F2& phim
 {
     const F2 da = v[1] - v[0], db = v[2] - v[1], dc = v[3] - v[2];
     const F2 dd = v[4] - v[3], de = v[5] - v[4];
-    cen_j = (fma2(F2(7.0f), db + dc, -(da + dd))) * F2(1.0f / 12.0f);
+    cen_j = fma2(F2(-7.0f), db + dc, da + dd) * F2(-1.0f / 12.0f);  // as in weno5_jp2
     // second differences S_{j-1} .. S_{j+2}
     const F2 Sa = db - da, Sb = dc - db, Sc = dd - dc, Sd = de - dd;
-    const F2 m4 = max2(max2(db * db, dc * dc), max2(dd * dd, de * de));
-    const F2 e = fma2(F2(1.2e-5f), max2(m4, da * da), F2(floor12));
+    const F2 m5 = max2(max2(max2(abs2(db), abs2(dc)), max2(abs2(dd), abs2(de))), abs2(da));
+    const F2 e = fma2(F2(1.2e-5f), m5 * m5, F2(floor12));
     const F2 g1 = Sa - Sb, g2 = Sb - Sc, g3 = Sc - Sd;
     const F2 e1 = g1 * g1, e2 = g2 * g2, e3 = g3 * g3;
-    const F2 f0 = fma2(F2(-3.0f), Sb, Sa), f1 = Sb + Sc, f2 = fma2(F2(3.0f), Sc, -Sd);
+    const F2 f0 = fma2(F2(-3.0f), Sb, Sa), f1 = Sb + Sc, f2 = fma2(F2(-3.0f), Sc, Sd);
     const F2 three(3.0f), thirteen(13.0f), two(2.0f);
     const F2 b0 = fma2(thirteen, e1, three * f0 * f0);
     const F2 b1 = fma2(thirteen, e2, three * f1 * f1);

@@ -1,12 +1,15 @@
 // stage_pair.cuh -- the tiled WENO5 stage body evaluating two consecutive
 // planes of the march per iteration with paired FP32 instructions.
 //
-// Same computation and the same per-node arithmetic order as
-// tiled_stage_body<.., WENO5, .., float> (stage_tiled.cuh); each thread
-// carries the nodes (s, ia, ib) and (s+1, ia, ib) together in F2 values, so
-// every add/mul/fma of the derivatives, the Hamiltonian and the combination
-// is issued once for both.  The plane tiles of s and s+1 are staged side by
-// side (double-buffered, four tiles), the marching window holds 2G+2 values.
+// Same computation as tiled_stage_body<.., WENO5, .., float>
+// (stage_tiled.cuh) with the same WENO5 arithmetic; each thread carries the
+// nodes (s, ia, ib) and (s+1, ia, ib) together in F2 values, so every
+// add/mul/fma of the derivatives, the Hamiltonian and the combination is
+// issued once for both.  Each axis' central costate and dissipation are
+// formed from the WENO5 parts (lf_axis2) rather than from the rounded
+// one-sided derivatives, so the two bodies agree to rounding, not bit for
+// bit.  The plane tiles of s and s+1 are staged side by side
+// (double-buffered, four tiles), the marching window holds 2G+2 values.
 #pragma once
 #include "pair2.cuh"
 #include "stage_tiled.cuh"
@@ -92,6 +95,13 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
                                     : a.alpha[k];
     const float dt = a.dt_from_ctl ? float(a.ctl->dt) : a.dt;
     const F2 cl(a.c_l * dt), cs(a.c_s), cn(a.c_n);
+    // alpha_k / (2 dx_k) and 1 / dx_k per axis (see lf_axis2)
+    F2 hax[NDIM], sx[NDIM];
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) {
+        hax[k] = F2(0.5f * alpha[k] * a.inv_dx[k]);
+        sx[k] = F2(a.inv_dx[k]);
+    }
     const float fl_s = weno_floor12(a.inv_dx[AS]);
     const float fl_a = weno_floor12(a.inv_dx[AA]);
     const float fl_b = weno_floor12(a.inv_dx[AB]);
@@ -193,37 +203,32 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
         }
         if (active) {
             const bool second = s + 1 < s_end;
-            F2 u[2 * G + 1], pm, pp, pbar[NDIM], diss(0.f);
+            F2 u[2 * G + 1], cen, phim, phip, pbar[NDIM], diss(0.f);
             if constexpr (FACES) {
                 // faces s + 1/2 (x) and s + 3/2 (y): values w[1..6] and w[2..7]
-                F2 fm, fp, c;
+                F2 fm;
 #pragma unroll
                 for (int o = 0; o < 6; ++o) u[o] = F2(w[o + 1], w[o + 2]);
-                weno5_face2(u, fl_s, fm, fp, c);
-                const F2 sx(a.inv_dx[AS]);
-                pm = (c - F2(phim_next, fm.x())) * sx;
-                pp = (c + fp) * sx;
+                weno5_face2(u, fl_s, fm, phip, cen);
+                phim = F2(phim_next, fm.x());
                 phim_next = fm.y();
             } else {
 #pragma unroll
                 for (int o = 0; o <= 2 * G; ++o) u[o] = F2(w[o], w[o + 1]);
-                deriv_weno5_jp2(u, a.inv_dx[AS], fl_s, pm, pp);
+                weno5_jp2(u, fl_s, cen, phim, phip);
             }
-            pbar[AS] = F2(0.5f) * (pp + pm);
-            diss = F2(0.5f * alpha[AS]) * (pp - pm);
+            lf_axis2(cen, phim, phip, sx[AS], hax[AS], pbar[AS], diss);
 #pragma unroll
             for (int o = 0; o <= 2 * G; ++o)
                 u[o] = F2(curA[(ty + o) * W + tx + G], curB[(ty + o) * W + tx + G]);
-            deriv_weno5_jp2(u, a.inv_dx[AA], fl_a, pm, pp);
-            pbar[AA] = F2(0.5f) * (pp + pm);
-            diss = fma2(F2(0.5f * alpha[AA]), pp - pm, diss);
+            weno5_jp2(u, fl_a, cen, phim, phip);
+            lf_axis2(cen, phim, phip, sx[AA], hax[AA], pbar[AA], diss);
 #pragma unroll
             for (int o = 0; o <= 2 * G; ++o)
                 u[o] = F2(curA[(ty + G) * W + tx + o], curB[(ty + G) * W + tx + o]);
             const F2 center = u[G];
-            deriv_weno5_jp2(u, a.inv_dx[AB], fl_b, pm, pp);
-            pbar[AB] = F2(0.5f) * (pp + pm);
-            diss = fma2(F2(0.5f * alpha[AB]), pp - pm, diss);
+            weno5_jp2(u, fl_b, cen, phim, phip);
+            lf_axis2(cen, phim, phip, sx[AB], hax[AB], pbar[AB], diss);
             if constexpr (NDIM == 4) {
                 const float* c0 = a.phi_s + s * sS + ia * sA + ib;
                 const float* c1 = c0 + (second ? sS : 0);
@@ -239,9 +244,8 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
                                       line_value<float, COH>(c1, outer + o, a.n[0], a.stride[0],
                                                  a.periodic[0]));
                 }
-                deriv_weno5_jp2(u, a.inv_dx[0], weno_floor12(a.inv_dx[0]), pm, pp);
-                pbar[0] = F2(0.5f) * (pp + pm);
-                diss = fma2(F2(0.5f * alpha[0]), pp - pm, diss);
+                weno5_jp2(u, weno_floor12(a.inv_dx[0]), cen, phim, phip);
+                lf_axis2(cen, phim, phip, sx[0], hax[0], pbar[0], diss);
             }
             x[AS] = F2(fmaf(float(s), a.h[AS], a.lo[AS]), fmaf(float(s + 1), a.h[AS], a.lo[AS]));
             const F2 Hv = hamiltonian_pair<DYN, NDIM>(x, pbar, a.prm, sth, cth);

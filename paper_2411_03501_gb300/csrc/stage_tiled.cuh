@@ -64,9 +64,12 @@ __device__ __forceinline__ void deriv_weno5_jp(const R* u, R inv_dx, R floor12, 
     const R d0 = u[4] - u[3], d1 = u[5] - u[4], d2 = u[6] - u[5];
     const R Sm2 = dm2 - dm3, Sm1 = dm1 - dm2, S0 = d0 - dm1, S1 = d1 - d0, S2 = d2 - d1;
     const R cen = (R(7) * (dm1 + d0) - (dm2 + d1)) * R(1.0 / 12.0);
-    const R m4 = rmax(rmax(dm2 * dm2, dm1 * dm1), rmax(d0 * d0, d1 * d1));
-    const R eL = R(1.2e-5) * rmax(m4, dm3 * dm3) + floor12;
-    const R eR = R(1.2e-5) * rmax(m4, d2 * d2) + floor12;
+    // max_k d_k^2 as (max_k |d_k|)^2: the same number (squaring rounds
+    // monotonically on [0, inf)), one multiply instead of six
+    const R m4 = rmax(rmax(rabs(dm2), rabs(dm1)), rmax(rabs(d0), rabs(d1)));
+    const R mL = rmax(m4, rabs(dm3)), mR = rmax(m4, rabs(d2));
+    const R eL = R(1.2e-5) * (mL * mL) + floor12;
+    const R eR = R(1.2e-5) * (mR * mR) + floor12;
     const R e1 = (Sm2 - Sm1) * (Sm2 - Sm1), e2 = (Sm1 - S0) * (Sm1 - S0);
     const R e3 = (S0 - S1) * (S0 - S1), e4 = (S1 - S2) * (S1 - S2);
     const R f0m = Sm2 - R(3) * Sm1, f1m = Sm1 + S0, f2m = R(3) * S0 - S1;
