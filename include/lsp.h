@@ -223,11 +223,12 @@ lsp_status lsp_hj_solve(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
  * second fastest and marches along the third over ch planes; each plane of
  * the tile is staged in shared memory with a 3-cell halo.  minb (2, 3 or 4)
  * selects the kernel variant compiled for that many CTAs per SM (register
- * budget 128, 80 or 64 per thread); pair = 1 (WENO5 only) selects the variant
- * that carries two consecutive planes per thread through paired FP32
- * instructions, pair = 2 the same with the marching axis' WENO5 terms
- * evaluated once per face (shared by the two nodes of the face; results
- * identical to pair = 1 bit for bit).
+ * budget 128, 80 or 64 per thread); pair = 1 (WENO5, ENO2, ENO3) selects
+ * the variant that carries two consecutive planes per thread through paired
+ * FP32 instructions, pair = 2 (WENO5 only) the same with the marching axis'
+ * WENO5 terms evaluated once per face (shared by the two nodes of the face;
+ * results identical to pair = 1 bit for bit).  A tile whose pair the scheme
+ * has no variant for makes the step use the generic kernel.
  *  lsp_set_tile(g, 0, 0, 0, 0, 0)   default: WENO5 16 x 16, 3 CTAs/SM, pair 2,
  *                                   chunks for ~3 waves (even length); other
  *                                   schemes 32 x 8, 3 CTAs/SM, chunks for ~2
@@ -242,13 +243,16 @@ lsp_status lsp_set_tile(lsp_grid* grid, int tb, int ta, int ch, int minb, int pa
 lsp_status lsp_get_tile(const lsp_grid* grid, const lsp_solve_opts* opts, int* tb, int* ta,
                         int* ch, int* minb, int* pair);
 
-/* Autotuner: time the first RK stage (phi -> workspace; phi is not
- * modified) for a set of tile shapes, chunk lengths, occupancy targets and,
- * for WENO5, the three kernel variants (up to 7 x 7 x 3 x 3 candidates, 3 timed
- * launches each) on this grid and
- * keep the fastest in the grid handle (reported through tb/ta/ch/minb/pair, which may
- * be NULL).  Waits for the GPU.  For grids without a tiled kernel it
- * selects the generic one (all -1).  LSP_EUNSUPPORTED for QUADRATIC. */
+/* Autotuner: time whole RK steps of the solve on a scratch copy of phi
+ * (phi is not modified; a copy of phi stands in for the tube target; two
+ * fields are allocated for the call, and without room for them the first
+ * stage alone is timed) for a set of tile shapes (7 fixed, 2 fitted to the
+ * grid), chunk lengths, occupancy targets and kernel variants (WENO5: pair 0,
+ * 1, 2; ENO2 and ENO3: pair 0, 1; up to 9 x 7 x 3 x 3 candidates), re-time the
+ * six fastest over longer windows and keep the best in the grid handle
+ * (reported through tb/ta/ch/minb/pair, which may be NULL).  Waits for the
+ * GPU.  For grids without a tiled kernel it selects the generic one (all
+ * -1).  LSP_EUNSUPPORTED for QUADRATIC. */
 lsp_status lsp_autotune(lsp_grid* grid, const lsp_solve_opts* opts, const void* phi,
                         void* workspace, size_t workspace_bytes, void* stream, int* tb, int* ta,
                         int* ch, int* minb, int* pair);

@@ -736,16 +736,50 @@ lsp_status lsp_autotune(lsp_grid* g, const lsp_solve_opts* o, const void* phi, v
     lsp_grid trial = *g;
     trial.gexec = nullptr;
     trial.capture_stream = nullptr;
+    // Candidates are timed on whole RK steps of a scratch copy of phi (the
+    // caller's field is never written), with a copy of phi standing in for
+    // the tube target: the later stages read the previous level and the
+    // target besides the stencil field, and single first stages (which read
+    // phi alone) ranked the tiles differently from the solve.  Without room
+    // for the two scratch fields the first stage alone is timed.
+    const size_t F = round256((size_t)g->npts * sizeof(float));
+    char* scratch = nullptr;
+    if (cudaMalloc(&scratch, 2 * F) != cudaSuccess) {
+        cudaGetLastError();
+        scratch = nullptr;
+    }
+    float* sphi = (float*)scratch;
+    float* stgt = scratch ? (float*)(scratch + F) : nullptr;
+    if (scratch && (cudaMemcpyAsync(sphi, phi, (size_t)g->npts * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, st) ||
+                    cudaMemcpyAsync(stgt, phi, (size_t)g->npts * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, st))) {
+        cudaFree(scratch);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(LSP_ECUDA, "autotune scratch copy");
+    }
     float best_ms = 1e30f;
     lsp::Tile best{0, 0, 0, 0, 0};
+    // the fastest few of the first round, re-timed over longer windows
+    constexpr int kFinal = 6;
+    float top_ms[kFinal];
+    lsp::Tile top[kFinal];
+    int ntop = 0;
     const double dt = cfl_dt_host(g, o->cfl, 0.0, INFINITY);
+    auto run_once = [&]() -> lsp_status {
+        if (scratch) return enqueue_step<float>(&trial, o, sphi, o->tube ? stgt : nullptr, dt, ws, st);
+        return enqueue_stage<float>(&trial, o, ctl, (const float*)phi, nullptr, nullptr, w1, dt,
+                                    0.0, 1.0, 1.0, false, st);
+    };
     for (int si = 0; si < nshapes; ++si) {
         const int* sh = shapes[si];
         for (int cand = 0; cand < 63; ++cand) {
             const int sp = splits[cand % 7];
             const int minb = 2 + (cand / 7) % 3;
             const int pair = cand / 21;
-            if (pair && o->scheme != LSP_WENO5) continue;
+            if (pair == 2 && o->scheme != LSP_WENO5) continue;
+            if (pair == 1 && o->scheme == LSP_UPWIND1) continue;
             const int nS = g->n[d - 3];
             lsp::Tile t{sh[0], sh[1], (nS + sp - 1) / sp, minb, pair};
             if (!lsp::tile_valid(d, o->scheme, t, g->n)) continue;
@@ -754,8 +788,7 @@ lsp_status lsp_autotune(lsp_grid* g, const lsp_solve_opts* o, const void* phi, v
             float ms_min = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, st);
-                s = enqueue_stage<float>(&trial, o, ctl, (const float*)phi, nullptr, nullptr, w1,
-                                         dt, 0.0, 1.0, 1.0, false, st);
+                s = run_once();
                 cudaEventRecord(e1, st);
                 if (s) break;
                 cudaEventSynchronize(e1);
@@ -764,15 +797,47 @@ lsp_status lsp_autotune(lsp_grid* g, const lsp_solve_opts* o, const void* phi, v
                 if (rep > 0 && ms < ms_min) ms_min = ms;  // first run warms up
             }
             if (s) break;
-            if (ms_min < best_ms) {
-                best_ms = ms_min;
-                best = t;
+            // keep the kFinal fastest, sorted
+            int pos = ntop < kFinal ? ntop++ : kFinal;
+            if (pos == kFinal && ms_min >= top_ms[kFinal - 1]) continue;
+            if (pos == kFinal) pos = kFinal - 1;
+            while (pos > 0 && top_ms[pos - 1] > ms_min) {
+                top_ms[pos] = top_ms[pos - 1];
+                top[pos] = top[pos - 1];
+                --pos;
             }
+            top_ms[pos] = ms_min;
+            top[pos] = t;
         }
         if (s) break;
     }
+    // second round: each finalist timed as the best of 3 windows of 3
+    // back-to-back runs (single runs of ~0.1-1 ms differ by a few %)
+    for (int i = 0; i < ntop && !s; ++i) {
+        trial.tile = top[i];
+        trial.tile_mode = 1;
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 3 && !s; ++rep) {
+            cudaEventRecord(e0, st);
+            for (int k = 0; k < 3 && !s; ++k) s = run_once();
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < ms_min) ms_min = ms;
+        }
+        if (!s && ms_min < best_ms) {
+            best_ms = ms_min;
+            best = top[i];
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (scratch) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        cudaFree(scratch);
+        if (!s && e != cudaSuccess) return cuda_fail(e, "autotune");
+    }
     if (s) return s;
     if (best.ch == 0) return fail(LSP_EUNSUPPORTED, "no valid tile for this grid");
     g->tile = best;

@@ -30,7 +30,10 @@ bool tile_valid(int ndim, int scheme, const Tile& t, const int* n)
     const int G = ghost_width(scheme);
     if (t.tb < 1 || t.ta < 1 || t.ch < 1 || t.tb * t.ta > 256) return false;
     if (t.minb < 2 || t.minb > 4) return false;
-    if (t.pair < 0 || t.pair > 2 || (t.pair != 0 && scheme != WENO5)) return false;
+    // pair 1: paired planes (WENO5, ENO2, ENO3); pair 2: WENO5 shared faces
+    if (t.pair < 0 || t.pair > 2) return false;
+    if (t.pair == 1 && scheme != WENO5 && scheme != ENO2 && scheme != ENO3) return false;
+    if (t.pair == 2 && scheme != WENO5) return false;
     // each thread stages at most 4 values of the haloed plane tile
     if ((t.ta + 2 * G) * (t.tb + 2 * G) > 4 * t.ta * t.tb) return false;
     const int nS = n[ndim - 3];

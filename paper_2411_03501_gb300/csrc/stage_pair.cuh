@@ -1,14 +1,15 @@
-// stage_pair.cuh -- the tiled WENO5 stage body evaluating two consecutive
-// planes of the march per iteration with paired FP32 instructions.
+// stage_pair.cuh -- the tiled stage body (WENO5, ENO2, ENO3) evaluating two
+// consecutive planes of the march per iteration with paired FP32
+// instructions.
 //
-// Same computation as tiled_stage_body<.., WENO5, .., float>
-// (stage_tiled.cuh) with the same WENO5 arithmetic; each thread carries the
-// nodes (s, ia, ib) and (s+1, ia, ib) together in F2 values, so every
-// add/mul/fma of the derivatives, the Hamiltonian and the combination is
-// issued once for both.  Each axis' central costate and dissipation are
-// formed from the WENO5 parts (lf_axis2) rather than from the rounded
-// one-sided derivatives, so the two bodies agree to rounding, not bit for
-// bit.  The plane tiles of s and s+1 are staged side by side
+// Same computation as tiled_stage_body<.., SCHEME, .., float>
+// (stage_tiled.cuh); each thread carries the nodes (s, ia, ib) and
+// (s+1, ia, ib) together in F2 values, so every add/mul/fma of the
+// derivatives, the Hamiltonian and the combination is issued once for both
+// (the ENO stencil choices are made per node, on the same differences as the
+// scalar body).  Each axis' central costate and dissipation are formed from
+// the scheme's parts (axis_pair) rather than from the rounded one-sided
+// derivatives, so the two bodies agree to rounding, not bit for bit.  The plane tiles of s and s+1 are staged side by side
 // (double-buffered, four tiles), the marching window holds 2G+2 values.
 #pragma once
 #include "pair2.cuh"
@@ -65,17 +66,41 @@ __device__ __forceinline__ F2 hamiltonian_pair(const F2* x, const F2* p, const f
     }
 }
 
-// FACES = true: the marching axis' derivatives come from shared faces
-// (weno5_face2): one face evaluation per node instead of two one-sided ones,
-// the left-biased correction of the next plane carried in a register.  The
-// results are bit-identical to FACES = false.
-template <int NDIM, int DYN, bool FACES = false, bool COH = false>
+// One axis of the paired LF rate from the window u[0..2G] of both nodes:
+// adds the axis' central costate to pbar and its dissipation to diss.
+// WENO5 delivers both multiplied by 6 (lf_axis2); ENO2/ENO3 as they are:
+// pbar = (p+ + p-)/2, dissipation alpha (p+ - p-)/2 from dx p-, dx p+.
+template <int SCHEME>
+__device__ __forceinline__ void axis_pair(const F2* u, float floor4, float inv_dx, float alpha,
+                                          F2& pbar, F2& diss)
+{
+    if constexpr (SCHEME == WENO5) {
+        F2 cen6, phim6, phip6;
+        weno5_jp2(u, floor4, cen6, phim6, phip6);
+        lf_axis2(cen6, phim6, phip6, F2(inv_dx), F2(0.5f * alpha * inv_dx), pbar, diss);
+    } else {
+        static_assert(SCHEME == ENO2 || SCHEME == ENO3, "paired ENO2, ENO3 or WENO5");
+        F2 am, ap;
+        if constexpr (SCHEME == ENO2) eno2_parts2(u, am, ap);
+        else eno3_parts2(u, am, ap);
+        pbar = (ap + am) * F2(0.5f * inv_dx);
+        diss = fma2(F2(0.5f * alpha * inv_dx), ap - am, diss);
+    }
+}
+
+// FACES = true (WENO5): the marching axis' derivatives come from shared
+// faces (weno5_face2): one face evaluation per node instead of two one-sided
+// ones, the left-biased correction of the next plane carried in a register.
+// The results are bit-identical to FACES = false.  SCHEME: WENO5, ENO2 or
+// ENO3.
+template <int NDIM, int DYN, bool FACES = false, bool COH = false, int SCHEME = WENO5>
 __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int TB, int TA, int bx,
                                                 int by, int chunk, int outer, int ch, float* tile,
                                                 int tx, int ty)
 {
     static_assert(NDIM == 3 || NDIM == 4, "paired planes need a marching axis");
-    constexpr int G = 3;
+    static_assert(SCHEME == WENO5 || !FACES, "shared faces are a WENO5 form");
+    constexpr int G = ghost_width(SCHEME);
     constexpr int AS = NDIM - 3, AA = NDIM - 2, AB = NDIM - 1;
     const int W = TB + 2 * G, H = TA + 2 * G, HW = H * W;
     const int nB = a.n[AB], nA = a.n[AA], nS = a.n[AS];
@@ -94,17 +119,15 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
         alpha[k] = a.alpha_from_ctl ? float(__longlong_as_double((long long)a.ctl->alpha_bits[k]))
                                     : a.alpha[k];
     const float dt = a.dt_from_ctl ? float(a.ctl->dt) : a.dt;
-    const F2 cl(a.c_l * dt), cs(a.c_s), cn(a.c_n);
-    // alpha_k / (2 dx_k) and 1 / dx_k per axis (see lf_axis2)
-    F2 hax[NDIM], sx[NDIM];
-#pragma unroll
-    for (int k = 0; k < NDIM; ++k) {
-        hax[k] = F2(0.5f * alpha[k] * a.inv_dx[k]);
-        sx[k] = F2(a.inv_dx[k]);
-    }
-    const float fl_s = weno_floor12(a.inv_dx[AS]);
-    const float fl_a = weno_floor12(a.inv_dx[AA]);
-    const float fl_b = weno_floor12(a.inv_dx[AB]);
+    // WENO5: the axes deliver 6 x the central costate and 6 x the
+    // dissipation (lf_axis2); the Hamiltonians are positively homogeneous in
+    // p (degree 1, the quadratic one degree 2, rescaled below), so the rate
+    // comes out as 6 L and the 1/6 goes into the stage's time coefficient.
+    constexpr float kRate = SCHEME == WENO5 ? 6.0f : 1.0f;
+    const F2 clk(a.c_l * dt * (1.0f / kRate)), cs(a.c_s), cn(a.c_n);
+    const float fl_s = weno_floor4(a.inv_dx[AS]);
+    const float fl_a = weno_floor4(a.inv_dx[AA]);
+    const float fl_b = weno_floor4(a.inv_dx[AB]);
 
     F2 x[NDIM];
     if constexpr (NDIM == 4) x[0] = F2(fmaf(float(outer), a.h[0], a.lo[0]));
@@ -203,32 +226,31 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
         }
         if (active) {
             const bool second = s + 1 < s_end;
-            F2 u[2 * G + 1], cen, phim, phip, pbar[NDIM], diss(0.f);
+            F2 u[2 * G + 1], pbar[NDIM], diss(0.f);
             if constexpr (FACES) {
                 // faces s + 1/2 (x) and s + 3/2 (y): values w[1..6] and w[2..7]
-                F2 fm;
+                F2 fm, cen, phip;
 #pragma unroll
                 for (int o = 0; o < 6; ++o) u[o] = F2(w[o + 1], w[o + 2]);
                 weno5_face2(u, fl_s, fm, phip, cen);
-                phim = F2(phim_next, fm.x());
+                const F2 phim(phim_next, fm.x());
                 phim_next = fm.y();
+                lf_axis2(cen, phim, phip, F2(a.inv_dx[AS]), F2(0.5f * alpha[AS] * a.inv_dx[AS]),
+                         pbar[AS], diss);
             } else {
 #pragma unroll
                 for (int o = 0; o <= 2 * G; ++o) u[o] = F2(w[o], w[o + 1]);
-                weno5_jp2(u, fl_s, cen, phim, phip);
+                axis_pair<SCHEME>(u, fl_s, a.inv_dx[AS], alpha[AS], pbar[AS], diss);
             }
-            lf_axis2(cen, phim, phip, sx[AS], hax[AS], pbar[AS], diss);
 #pragma unroll
             for (int o = 0; o <= 2 * G; ++o)
                 u[o] = F2(curA[(ty + o) * W + tx + G], curB[(ty + o) * W + tx + G]);
-            weno5_jp2(u, fl_a, cen, phim, phip);
-            lf_axis2(cen, phim, phip, sx[AA], hax[AA], pbar[AA], diss);
+            axis_pair<SCHEME>(u, fl_a, a.inv_dx[AA], alpha[AA], pbar[AA], diss);
 #pragma unroll
             for (int o = 0; o <= 2 * G; ++o)
                 u[o] = F2(curA[(ty + G) * W + tx + o], curB[(ty + G) * W + tx + o]);
             const F2 center = u[G];
-            weno5_jp2(u, fl_b, cen, phim, phip);
-            lf_axis2(cen, phim, phip, sx[AB], hax[AB], pbar[AB], diss);
+            axis_pair<SCHEME>(u, fl_b, a.inv_dx[AB], alpha[AB], pbar[AB], diss);
             if constexpr (NDIM == 4) {
                 const float* c0 = a.phi_s + s * sS + ia * sA + ib;
                 const float* c1 = c0 + (second ? sS : 0);
@@ -244,14 +266,15 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
                                       line_value<float, COH>(c1, outer + o, a.n[0], a.stride[0],
                                                  a.periodic[0]));
                 }
-                weno5_jp2(u, weno_floor12(a.inv_dx[0]), cen, phim, phip);
-                lf_axis2(cen, phim, phip, sx[0], hax[0], pbar[0], diss);
+                axis_pair<SCHEME>(u, weno_floor4(a.inv_dx[0]), a.inv_dx[0], alpha[0], pbar[0], diss);
             }
             x[AS] = F2(fmaf(float(s), a.h[AS], a.lo[AS]), fmaf(float(s + 1), a.h[AS], a.lo[AS]));
-            const F2 Hv = hamiltonian_pair<DYN, NDIM>(x, pbar, a.prm, sth, cth);
+            F2 Hv = hamiltonian_pair<DYN, NDIM>(x, pbar, a.prm, sth, cth);  // kRate x H
+            if constexpr (SCHEME == WENO5 && DYN == QUADRATIC)
+                Hv = Hv * F2(1.0f / 6.0f);  // 36 H -> 6 H
             const F2 L = diss - Hv;
             const int idx = base_outer + s * sS + ia * sA + ib;
-            F2 v = fma2(cs, center, cl * L);
+            F2 v = fma2(cs, center, clk * L);
             if (a.phi_n)
                 v = fma2(cn, F2(ld_phin<COH>(a.phi_n + idx), second ? ld_phin<COH>(a.phi_n + idx + sS) : 0.f), v);
             if (a.tube) v = min2(v, F2(__ldg(a.target + idx), second ? __ldg(a.target + idx + sS) : 0.f));
@@ -265,14 +288,14 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
     if (nonfinite) atomicOr(&a.ctl->flags, kFlagNonFinite);
 }
 
-// Single-problem launch of the paired body (WENO5, FP32): blockDim = (tb,
-// ta); gridDim = (ceil(nB/tb), ceil(nA/ta), nchunks * nOuter); ch is even.
-template <int NDIM, int DYN, int MINB, bool FACES>
+// Single-problem launch of the paired body (FP32): blockDim = (tb, ta);
+// gridDim = (ceil(nB/tb), ceil(nA/ta), nchunks * nOuter).
+template <int NDIM, int DYN, int MINB, bool FACES, int SCHEME = WENO5>
 __global__ void __launch_bounds__(256, MINB) stage_pair_kernel(StageArgs<float> a, int ch, int nchunks)
 {
     extern __shared__ unsigned char smem_raw[];
     float* tile = reinterpret_cast<float*>(smem_raw);
-    tiled_pair_body<NDIM, DYN, FACES>(a, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y,
+    tiled_pair_body<NDIM, DYN, FACES, false, SCHEME>(a, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y,
                                blockIdx.z % nchunks, blockIdx.z / nchunks, ch, tile, threadIdx.x,
                                threadIdx.y);
 }

@@ -92,6 +92,13 @@ __device__ __forceinline__ R weno_floor12(R inv_dx)
     return R(12) * Num<R>::eps_floor(inv_dx);
 }
 
+// 4 x the floor, for the indicators scaled by 1/3 of the paired form (pair2.cuh).
+template <typename R>
+__device__ __forceinline__ R weno_floor4(R inv_dx)
+{
+    return R(4) * Num<R>::eps_floor(inv_dx);
+}
+
 template <int SCHEME, typename R>
 __device__ __forceinline__ void deriv_fast(const R* u, R inv_dx, R floor12, R& pm, R& pp)
 {

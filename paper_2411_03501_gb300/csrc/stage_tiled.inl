@@ -18,11 +18,13 @@ static cudaError_t tiled_one(const StageArgs<float>& a, const Tile& t, cudaStrea
     const size_t smem = 2 * sizeof(float) * (t.ta + 2 * G) * (t.tb + 2 * G);
     // (local coefficients and the variational clip never reach this file:
     // launch_stage_tiled sends them to stage_tiled_local.cu)
-    if constexpr (SCHEME == WENO5) {
+    if constexpr (SCHEME == WENO5 || SCHEME == ENO2 || SCHEME == ENO3) {
         if (t.pair == 1) {
-            stage_pair_kernel<NDIM, DYN, LSP_MINB, false><<<grid, block, 2 * smem, s>>>(a, t.ch, nchunks);
+            stage_pair_kernel<NDIM, DYN, LSP_MINB, false, SCHEME><<<grid, block, 2 * smem, s>>>(a, t.ch, nchunks);
             return cudaGetLastError();
         }
+    }
+    if constexpr (SCHEME == WENO5) {
         if (t.pair == 2) {
             stage_pair_kernel<NDIM, DYN, LSP_MINB, true><<<grid, block, 2 * smem, s>>>(a, t.ch, nchunks);
             return cudaGetLastError();
