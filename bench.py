@@ -100,7 +100,10 @@ def algorithmic(spec) -> tuple[float, float]:
     """(bytes, flops) per node per stage, averaged over the stages of a step."""
     word = 8 if spec["dtype"] == "f64" else 4
     rk = spec["rk"]
-    words = {1: 2.0, 2: 2.5, 3: 3.0}[rk]
+    # fields read + written by the stages of one step (the last stage also
+    # reads the previous level, the tube's stage the target):
+    # RK1 phi -> W1; RK2 +(W1, phi -> phi); RK3 +(W1, phi -> W2), (W2, phi -> phi)
+    words = {1: 2.0, 2: 5.0 / 2, 3: 8.0 / 3}[rk]
     if spec.get("tube"):
         words += 1.0 / rk
     d = spec["ndim"]
