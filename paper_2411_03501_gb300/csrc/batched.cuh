@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kBatchTB * kBatchTA, 3)
 {
     constexpr int G = ghost_width(SCHEME);
     __shared__ StageArgs<float> sa;
-    __shared__ float tile[batch_tile_floats<SCHEME, LOCAL>()];
+    __shared__ __align__(16) float tile[batch_tile_floats<SCHEME, LOCAL>()];
     const int p = block_prob[blockIdx.x];
     const BatchProblem& P = probs[p];
     const int tid = threadIdx.y * kBatchTB + threadIdx.x;
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kBatchTB * kBatchTA, 3)
 {
     constexpr int G = ghost_width(SCHEME);
     __shared__ StageArgs<float> sa;
-    __shared__ float tile[batch_tile_floats<SCHEME, LOCAL>()];
+    __shared__ __align__(16) float tile[batch_tile_floats<SCHEME, LOCAL>()];
     __shared__ int s_p, s_local, s_stop;
     const int tid = threadIdx.y * kBatchTB + threadIdx.x;
     const long long total = segs[nseg].item_start;

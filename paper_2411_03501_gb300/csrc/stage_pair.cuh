@@ -9,8 +9,10 @@
 // (the ENO stencil choices are made per node, on the same differences as the
 // scalar body).  Each axis' central costate and dissipation are formed from
 // the scheme's parts (axis_pair) rather than from the rounded one-sided
-// derivatives, so the two bodies agree to rounding, not bit for bit.  The plane tiles of s and s+1 are staged side by side
-// (double-buffered, four tiles), the marching window holds 2G+2 values.
+// derivatives, so the two bodies agree to rounding, not bit for bit.  The
+// plane tiles of s and s+1 are staged interleaved (a float2 per node, one
+// 64-bit shared access for both planes), double-buffered; the marching
+// window holds 2G+2 values.
 #pragma once
 #include "pair2.cuh"
 #include "stage_tiled.cuh"
@@ -207,14 +209,12 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
     }
 
     for (int s = s_begin; s < s_end; s += 2) {
-        float* curA = tile + (((s - s_begin) >> 1) & 1) * (2 * HW);
-        float* curB = curA + HW;
+        // planes s and s+1 interleaved: one 64-bit shared access moves a
+        // node's value on both planes, already in the pair layout
+        float2* cur = reinterpret_cast<float2*>(tile) + (((s - s_begin) >> 1) & 1) * HW;
 #pragma unroll
         for (int k = 0; k < MAXE; ++k)
-            if (((kinds >> (2 * k)) & 3u) != 3u) {
-                curA[tid + k * nthr] = pfA[k];
-                curB[tid + k * nthr] = pfB[k];
-            }
+            if (((kinds >> (2 * k)) & 3u) != 3u) cur[tid + k * nthr] = make_float2(pfA[k], pfB[k]);
         w[2 * G] = wnA;
         w[2 * G + 1] = wnB;
         __syncthreads();  // planes s, s+1 staged; the other buffer pair is free
@@ -244,11 +244,11 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
             }
 #pragma unroll
             for (int o = 0; o <= 2 * G; ++o)
-                u[o] = F2(curA[(ty + o) * W + tx + G], curB[(ty + o) * W + tx + G]);
+                u[o] = F2(cur[(ty + o) * W + tx + G]);
             axis_pair<SCHEME>(u, fl_a, a.inv_dx[AA], alpha[AA], pbar[AA], diss);
 #pragma unroll
             for (int o = 0; o <= 2 * G; ++o)
-                u[o] = F2(curA[(ty + G) * W + tx + o], curB[(ty + G) * W + tx + o]);
+                u[o] = F2(cur[(ty + G) * W + tx + o]);
             const F2 center = u[G];
             axis_pair<SCHEME>(u, fl_b, a.inv_dx[AB], alpha[AB], pbar[AB], diss);
             if constexpr (NDIM == 4) {
@@ -293,8 +293,8 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
 template <int NDIM, int DYN, int MINB, bool FACES, int SCHEME = WENO5>
 __global__ void __launch_bounds__(256, MINB) stage_pair_kernel(StageArgs<float> a, int ch, int nchunks)
 {
-    extern __shared__ unsigned char smem_raw[];
-    float* tile = reinterpret_cast<float*>(smem_raw);
+    extern __shared__ __align__(16) unsigned char smem_pair[];
+    float* tile = reinterpret_cast<float*>(smem_pair);
     tiled_pair_body<NDIM, DYN, FACES, false, SCHEME>(a, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y,
                                blockIdx.z % nchunks, blockIdx.z / nchunks, ch, tile, threadIdx.x,
                                threadIdx.y);
