@@ -148,27 +148,41 @@ __device__ __forceinline__ void grad_weno5(const R* u7, R inv_dx, R floor12, R* 
         add_D(gp, q - 2, cw[q] * inv_dx);
     }
     // regulariser e = 1.2e-5 max(D^2 over the side's five differences) + floor;
-    // argmax frozen (the first of equal values)
+    // argmax frozen (the first of equal values).  The maxima are tracked by
+    // value and the argmax only selects among unrolled updates, so that no
+    // array is indexed at run time (that would place D, gm and gp in local
+    // memory).
     int mL = 0, mR = 1;
+    R DL = D[0], DL2 = D[0] * D[0], DR = D[1], DR2 = D[1] * D[1];
 #pragma unroll
-    for (int m = 1; m < 5; ++m)
-        if (D[m] * D[m] > D[mL] * D[mL]) mL = m;
+    for (int m = 1; m < 5; ++m) {
+        const R q = D[m] * D[m];
+        if (q > DL2) { DL2 = q; DL = D[m]; mL = m; }
+    }
 #pragma unroll
-    for (int m = 2; m < 6; ++m)
-        if (D[m] * D[m] > D[mR] * D[mR]) mR = m;
-    const R eL = R(1.2e-5) * D[mL] * D[mL] + floor12;
-    const R eR = R(1.2e-5) * D[mR] * D[mR] + floor12;
+    for (int m = 2; m < 6; ++m) {
+        const R q = D[m] * D[m];
+        if (q > DR2) { DR2 = q; DR = D[m]; mR = m; }
+    }
+    const R eL = R(1.2e-5) * DL * DL + floor12;
+    const R eR = R(1.2e-5) * DR * DR + floor12;
     R g4[4], ge;
     // p- = (cen - Phi(S_-2, S_-1, S_0, S_1)) / dx
     weno_phi_grad(S[0], S[1], S[2], S[3], eL, g4, &ge);
 #pragma unroll
     for (int q = 0; q < 4; ++q) add_S(gm, q - 2, -g4[q] * inv_dx);
-    add_D(gm, mL - 3, -ge * R(2.4e-5) * D[mL] * inv_dx);
+    const R wL = -ge * R(2.4e-5) * DL * inv_dx;
+#pragma unroll
+    for (int m = 0; m < 5; ++m)
+        if (m == mL) add_D(gm, m - 3, wL);
     // p+ = (cen + Phi(S_2, S_1, S_0, S_-1)) / dx
     weno_phi_grad(S[4], S[3], S[2], S[1], eR, g4, &ge);
 #pragma unroll
     for (int q = 0; q < 4; ++q) add_S(gp, 2 - q, g4[q] * inv_dx);
-    add_D(gp, mR - 3, ge * R(2.4e-5) * D[mR] * inv_dx);
+    const R wR = ge * R(2.4e-5) * DR * inv_dx;
+#pragma unroll
+    for (int m = 1; m < 6; ++m)
+        if (m == mR) add_D(gp, m - 3, wR);
 }
 
 template <int SCHEME, typename R>
