@@ -235,7 +235,7 @@ lsp_status lsp_hj_solve(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
  *                                   waves
  *  lsp_set_tile(g, -1, 0, 0, 0, 0)  always use the generic kernel
  *  lsp_set_tile(g, tb, ta, ch, minb, pair) explicit; LSP_EINVAL unless
- *        tb*ta <= 256, the haloed tile fits 4 values per thread, the launch
+ *        tb*ta <= 256, the haloed tile fits 3 values per thread, the launch
  *        has <= 65535 z-blocks, minb is 2, 3 or 4 and pair is 0, 1 or 2.
  * lsp_get_tile reports the tile a step with `opts` would use (all -1 when
  * the generic kernel runs). */

@@ -34,8 +34,9 @@ bool tile_valid(int ndim, int scheme, const Tile& t, const int* n)
     if (t.pair < 0 || t.pair > 2) return false;
     if (t.pair == 1 && scheme != WENO5 && scheme != ENO2 && scheme != ENO3) return false;
     if (t.pair == 2 && scheme != WENO5) return false;
-    // each thread stages at most 4 values of the haloed plane tile
-    if ((t.ta + 2 * G) * (t.tb + 2 * G) > 4 * t.ta * t.tb) return false;
+    // each thread stages at most 3 values of the haloed plane tile (MAXE of
+    // the tiled bodies; every shape the autotuner tries qualifies)
+    if ((t.ta + 2 * G) * (t.tb + 2 * G) > 3 * t.ta * t.tb) return false;
     const int nS = n[ndim - 3];
     const long long nz = (long long)((nS + t.ch - 1) / t.ch) * (ndim == 4 ? n[0] : 1);
     return nz <= 65535;

@@ -144,7 +144,7 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
 #pragma unroll
     for (int o = -G; o < G; ++o) w[o + G] = line_value<float, COH>(col, s_begin + o, nS, sS, a.periodic[AS]);
 
-    constexpr int MAXE = 4;
+    constexpr int MAXE = 3;
     int e_off[MAXE];
     unsigned kinds = 0;
 #pragma unroll

@@ -199,10 +199,10 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
             w[o + G] = line_value<R, COH>(col, s_begin + o, nS, sS, a.periodic[AS]);
     }
 
-    // This thread's share of the plane tile (with halo): at most 4 slots.
+    // This thread's share of the plane tile (with halo): at most 3 slots.
     // Kinds, packed 2 bits per slot: 0 interior, 1 ghost along B, 2 ghost
     // along A, 3 corner (never read by the axis stencils) or unused.
-    constexpr int MAXE = 4;
+    constexpr int MAXE = 3;
     int e_off[MAXE];
     unsigned kinds = 0;
 #pragma unroll
