@@ -281,8 +281,14 @@ struct AdjArgs {
     int npts;
 };
 
+// 3 CTAs of 256 per SM in FP32: the kernel fits 80 registers without spills
+// (left to itself the compiler takes 128 and runs 2 CTAs per SM; 64
+// registers spill); FP64 (the oracle comparisons) keeps 2.
+template <typename R>
+constexpr int adj_a_min_blocks() { return sizeof(R) == 4 ? 3 : 2; }
+
 template <int NDIM, int SCHEME, int DYN, typename R>
-__global__ void __launch_bounds__(256) adj_stage_a(AdjArgs<R> a)
+__global__ void __launch_bounds__(256, adj_a_min_blocks<R>()) adj_stage_a(AdjArgs<R> a)
 {
     constexpr int G = ghost_width(SCHEME);
     // per-thread partial sums in the field precision (a thread visits a few

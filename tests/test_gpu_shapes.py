@@ -12,6 +12,7 @@ from paper_2411_03501_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 SPECS = {
+    1: W.problem(1, [53], [-3], [2], [False], "eno2", "normal_speed", [1.0]),
     2: W.problem(2, [37, 29], [-2, -1], [2, 1.5], [False, True], "eno2", "normal_speed", [1.0]),
     3: W.problem(3, [21, 17, 19], [-6, -10, 0], [20, 10, 2 * np.pi], [False, False, True], "eno2",
                  "normal_speed", [1.0]),
@@ -39,7 +40,7 @@ def _check(got, want, dtype, scale):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
-@pytest.mark.parametrize("ndim", [2, 3, 4])
+@pytest.mark.parametrize("ndim", [1, 2, 3, 4])
 def test_primitives_match_oracle(ndim, dtype):
     spec = SPECS[ndim]
     g = _grid(spec)
@@ -49,13 +50,15 @@ def test_primitives_match_oracle(ndim, dtype):
     lin = np.sqrt(ndim) * (X + 1.0) + 2.0  # distances, coordinates, centre, radius
     B.lsp_shape_sphere(g, out, c, 1.7)
     _check(out, S.sphere(spec, c, 1.7), dtype, lin)
-    B.lsp_shape_sphere(g, out, c, 1.2, ignore=(ndim - 1,))
-    _check(out, S.sphere(spec, c, 1.2, ignore=(ndim - 1,)), dtype, lin)
+    if ndim > 1:  # (ignoring the only dimension of a 1-D grid leaves no distance)
+        B.lsp_shape_sphere(g, out, c, 1.2, ignore=(ndim - 1,))
+        _check(out, S.sphere(spec, c, 1.2, ignore=(ndim - 1,)), dtype, lin)
     lo, hi = [-1.0, -0.5, 0.5, 0.2][:ndim], [1.5, 0.8, 3.0, 1.1][:ndim]
     B.lsp_shape_box(g, out, lo, hi)
     _check(out, S.box(spec, lo, hi), dtype, lin)
-    B.lsp_shape_box(g, out, lo, hi, ignore=(0,))
-    _check(out, S.box(spec, lo, hi, ignore=(0,)), dtype, lin)
+    if ndim > 1:
+        B.lsp_shape_box(g, out, lo, hi, ignore=(0,))
+        _check(out, S.box(spec, lo, hi, ignore=(0,)), dtype, lin)
     w = [1.0, 4.0, 9.0, 2.0][:ndim]
     B.lsp_shape_quadric(g, out, c, w, 2.5)
     _check(out, S.quadric(spec, c, w, 2.5), dtype, sum(w) * (X + 1.0) ** 2 + 2.5)
@@ -95,3 +98,18 @@ def test_shape_argument_errors():
         with pytest.raises(B.LspError) as e:
             call()
         assert e.value.status == B.LSP_EINVAL
+
+
+def test_large_grid_node_coordinates():
+    """A 3-D grid of 16.6 M nodes (indices above 2^24, ragged axis lengths):
+    the node index split by the axis lengths (multiply-high division) gives
+    every node's coordinates, checked through a sphere in FP32 against the
+    oracle at every node."""
+    spec = W.problem(3, [257, 255, 253], [-6, -10, 0], [20, 10, 2 * np.pi], [False, False, True],
+                     "eno2", "normal_speed", [1.0])
+    g = _grid(spec)
+    out = torch.empty(tuple(spec["n"]), dtype=torch.float32, device="cuda")
+    c = [0.3, -0.4, 1.0]
+    B.lsp_shape_sphere(g, out, c, 1.2)
+    _check(out, S.sphere(spec, c, 1.2), torch.float32, np.sqrt(3) * 21.0 + 2.0)
+
