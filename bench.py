@@ -577,6 +577,7 @@ def run_adjoint(args, rank: int, world: int, local_rank: int):
     import numpy as np
     import torch
 
+    from paper_2411_03501_gb300 import binding as B
     from paper_2411_03501_gb300 import build as BLD
     from paper_2411_03501_gb300 import workloads as W
     from paper_2411_03501_gb300.autograd import HJTube
@@ -596,6 +597,11 @@ def run_adjoint(args, rank: int, world: int, local_rank: int):
     sdf, q = h_sdf.cuda(), h_q.cuda()
     tube = HJTube(spec, nsteps=nsteps)
     stream = torch.cuda.current_stream()
+    if args.tile:  # a fixed tile (the capture commands use the autotuner's choice)
+        tile = tuple(int(v) for v in args.tile.split(","))
+        B.lsp_set_tile(tube.grid, *tile)
+    else:
+        tile = tube.autotune(sdf - 5.0) if args.autotune else None
 
     def grad_step(sdf_d, q_d):
         base = torch.tensor([5.0, 5.0, 1.0], dtype=torch.float64, requires_grad=True)
@@ -623,6 +629,8 @@ def run_adjoint(args, rank: int, world: int, local_rank: int):
     ms = sum(a.elapsed_time(b) for a, b in ev)
     # plain forward of the same 200 steps (one checkpoint: a single copy)
     plain = HJTube(spec, nsteps=nsteps, ncheck=1)
+    if tile is not None:
+        B.lsp_set_tile(plain.grid, *tile)
     params = torch.tensor(spec["params"], dtype=torch.float64)
     tgt = sdf - 5.0
     with torch.no_grad():
@@ -657,6 +665,7 @@ def run_adjoint(args, rank: int, world: int, local_rank: int):
         "data": "synthetic",
         "config": {"workload": "adjoint_air3d_129^3_200xrk3_f32", "points": npts,
                    "rk_steps": nsteps, "checkpoints": tube.ncheck or int(np.ceil(np.sqrt(nsteps))),
+                   "tile": list(tile) if tile is not None else None,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "fields (8.6 MB each) partly L2-resident; no flush",
                    "plain_forward_value": units / (fwd_ms / 1e3),

@@ -85,6 +85,15 @@ class HJTube:
             B.lsp_set_dynamics(self.grid, self.spec["dyn"], p)
             self._params = p
 
+    def autotune(self, phi):
+        """Pick the stage kernel's tile for this grid (lsp_autotune, timed on
+        whole RK steps of a scratch copy of phi; phi is not modified).  The
+        forward, the recomputed segments and the stage inputs of the reverse
+        sweep all run with it.  Returns (tb, ta, ch, minb, pair)."""
+        nbytes = B.lsp_workspace_size(self.grid, self.opts)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=phi.device)
+        return B.lsp_autotune(self.grid, self.opts, phi, ws)
+
     def __call__(self, phi0, target, params):
         return _SolveFn.apply(phi0, target, params, self)
 
