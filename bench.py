@@ -248,7 +248,8 @@ def run_reference(args, rank: int, world: int):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": spec["name"], "points": npts, "parallelism": "replicas",
+        "config": {"workload": spec["name"], "points": npts,
+                   "parallelism": "single" if world == 1 else f"rank 0 alone of {world}",
                    "l2": "n/a (host)"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
                          "sample": sample},
