@@ -94,8 +94,10 @@ __device__ __forceinline__ void axis_pair(const F2* u, float floor4, float inv_d
 // faces (weno5_face2): one face evaluation per node instead of two one-sided
 // ones, the left-biased correction of the next plane carried in a register.
 // The results are bit-identical to FACES = false.  SCHEME: WENO5, ENO2 or
-// ENO3.
-template <int NDIM, int DYN, bool FACES = false, bool COH = false, int SCHEME = WENO5>
+// ENO3.  VARFORM: the rate of the variational form min[0, H] (Sec. VI-A,
+// Eq. 30), clipped at zero (for WENO5 the clip acts on 6 L, the same sign).
+template <int NDIM, int DYN, bool FACES = false, bool COH = false, int SCHEME = WENO5,
+          bool VARFORM = false>
 __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int TB, int TA, int bx,
                                                 int by, int chunk, int outer, int ch, float* tile,
                                                 int tx, int ty)
@@ -272,7 +274,8 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
             F2 Hv = hamiltonian_pair<DYN, NDIM>(x, pbar, a.prm, sth, cth);  // kRate x H
             if constexpr (SCHEME == WENO5 && DYN == QUADRATIC)
                 Hv = Hv * F2(1.0f / 6.0f);  // 36 H -> 6 H
-            const F2 L = diss - Hv;
+            F2 L = diss - Hv;
+            if constexpr (VARFORM) L = min2(L, F2(0.f));
             const int idx = base_outer + s * sS + ia * sA + ib;
             F2 v = fma2(cs, center, clk * L);
             if (a.phi_n)
@@ -290,12 +293,12 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
 
 // Single-problem launch of the paired body (FP32): blockDim = (tb, ta);
 // gridDim = (ceil(nB/tb), ceil(nA/ta), nchunks * nOuter).
-template <int NDIM, int DYN, int MINB, bool FACES, int SCHEME = WENO5>
+template <int NDIM, int DYN, int MINB, bool FACES, int SCHEME = WENO5, bool VARFORM = false>
 __global__ void __launch_bounds__(256, MINB) stage_pair_kernel(StageArgs<float> a, int ch, int nchunks)
 {
     extern __shared__ __align__(16) unsigned char smem_pair[];
     float* tile = reinterpret_cast<float*>(smem_pair);
-    tiled_pair_body<NDIM, DYN, FACES, false, SCHEME>(a, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y,
+    tiled_pair_body<NDIM, DYN, FACES, false, SCHEME, VARFORM>(a, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y,
                                blockIdx.z % nchunks, blockIdx.z / nchunks, ch, tile, threadIdx.x,
                                threadIdx.y);
 }
