@@ -816,7 +816,8 @@ def main():
     ap.add_argument("--workload", default="air3d_201")
     ap.add_argument("--graph", type=int, default=0)
     ap.add_argument("--cpu-baseline", type=int, default=1)
-    ap.add_argument("--outdir", default=os.path.join(ROOT, "gpurun_out"))
+    ap.add_argument("--outdir", default=os.path.join(ROOT, "bench_out"),
+                    help="where the clock samples of the timed region are written")
     ap.add_argument("--mode", default="solve", choices=["solve", "steps"])
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--tile", default="", help="tb,ta,ch,minb: fixed tile instead of autotuning")

@@ -2,7 +2,7 @@
  * lsp_oracle.c -- plain, slow, FP64 CPU oracle for the explicit Hamilton-Jacobi
  * level-set integrator of "LevelSetPy" (arXiv 2411.03501).
  *
- * TEST INFRASTRUCTURE ONLY.  This file is the yardstick the GPU path is judged
+ * TEST INFRASTRUCTURE ONLY.  This file is the yardstick the GPU path is checked
  * against.  It is called from tests/, from the smoke check and from the CPU
  * baseline leg of the benchmark; the product path never links or calls it, and
  * it shares no code, header, table or constant with the CUDA sources.
@@ -121,8 +121,8 @@ int orc_ghost_width(int scheme)
 }
 
 /* Fill one extended line u[-G .. n-1+G] (stored at offset G) from the n node
- * values of a grid line.  Sec. III-B: boundary conditions are "grafted in" by
- * populating ghost cells.  Periodic: wrap around.  Otherwise (reading; the
+ * values of a grid line.  Sec. III-B: boundary conditions enter through the
+ * ghost cells that extend each line.  Periodic: wrap around.  Otherwise (reading; the
  * paper names no other condition): linear extrapolation from the two nodes
  * nearest the boundary, u[-k] = u[0] + k (u[0] - u[1]). */
 static void fill_line(const double* line, int64_t n, int G, int periodic, double* ext)
