@@ -41,26 +41,27 @@ __device__ __forceinline__ void batch_stage_args(const BatchProblem& P, int step
 }
 
 // The body of one tile of a 3-D / 4-D problem: the paired shared-face body
-// for the global-LF WENO5 stage (as single-problem solves run it by
-// default), the scalar body otherwise.
+// for the WENO5 stage (as single-problem solves run it by default; its local
+// variant for local coefficients or the clip, state-only bounds), the scalar
+// body otherwise.
 template <int NDIM, int SCHEME, int DYN, bool COH, bool LOCAL>
 __device__ __forceinline__ void batch_body(const StageArgs<float>& sa, int bx, int by, int chunk,
                                            int outer, int ch, float* tile, int tx, int ty)
 {
-    if constexpr (SCHEME == WENO5 && !LOCAL)
-        tiled_pair_body<NDIM, DYN, true, COH>(sa, kBatchTB, kBatchTA, bx, by, chunk, outer, ch,
-                                              tile, tx, ty);
+    if constexpr (SCHEME == WENO5 && (!LOCAL || DYN != QUADRATIC))
+        tiled_pair_body<NDIM, DYN, true, COH, WENO5, LOCAL>(sa, kBatchTB, kBatchTA, bx, by, chunk,
+                                                            outer, ch, tile, tx, ty);
     else
         tiled_stage_body<NDIM, SCHEME, DYN, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by,
                                                                chunk, outer, ch, tile, tx, ty);
 }
 
 // Shared tile of a batched CTA: two double-buffered planes, four for the
-// paired body.
+// paired body (WENO5).
 template <int SCHEME, bool LOCAL>
 __host__ __device__ constexpr int batch_tile_floats()
 {
-    return ((SCHEME == WENO5 && !LOCAL) ? 4 : 2) * (kBatchTA + 2 * ghost_width(SCHEME)) *
+    return (SCHEME == WENO5 ? 4 : 2) * (kBatchTA + 2 * ghost_width(SCHEME)) *
            (kBatchTB + 2 * ghost_width(SCHEME));
 }
 

@@ -45,9 +45,10 @@ bool tile_valid(int ndim, int scheme, const Tile& t, const int* n)
 cudaError_t launch_stage_tiled(int ndim, int scheme, int dyn, const StageArgs<float>& a,
                                const Tile& t, cudaStream_t s)
 {
-    // local coefficients, and the variational clip outside the WENO5
-    // shared-face kernel (which has a clipped variant), run the local bodies
-    if (a.local_alpha || (a.varform && !(scheme == WENO5 && t.pair == 2)))
+    // local coefficients and the variational clip run the scalar local
+    // bodies, except on the WENO5 shared-face tile with state-only bounds,
+    // whose kernel has a local variant
+    if ((a.local_alpha || a.varform) && !(scheme == WENO5 && t.pair == 2 && dyn != QUADRATIC))
         return launch_stage_tiled_local(ndim, scheme, dyn, a, t, s);
     switch (t.minb) {
     case 2: return launch_stage_tiled_m<2>(ndim, scheme, dyn, a, t, s);

@@ -69,24 +69,25 @@ __device__ __forceinline__ F2 hamiltonian_pair(const F2* x, const F2* p, const f
 }
 
 // One axis of the paired LF rate from the window u[0..2G] of both nodes:
-// adds the axis' central costate to pbar and its dissipation to diss.
-// WENO5 delivers both multiplied by 6 (lf_axis2); ENO2/ENO3 as they are:
-// pbar = (p+ + p-)/2, dissipation alpha (p+ - p-)/2 from dx p-, dx p+.
+// adds the axis' central costate to pbar and its dissipation to diss, with
+// hax = alpha / (2 dx) per node.  WENO5 delivers both multiplied by 6
+// (lf_axis2); ENO2/ENO3 as they are: pbar = (p+ + p-)/2, dissipation
+// alpha (p+ - p-)/2 from dx p-, dx p+.
 template <int SCHEME>
-__device__ __forceinline__ void axis_pair(const F2* u, float floor4, float inv_dx, float alpha,
+__device__ __forceinline__ void axis_pair(const F2* u, float floor4, float inv_dx, F2 hax,
                                           F2& pbar, F2& diss)
 {
     if constexpr (SCHEME == WENO5) {
         F2 cen6, phim6, phip6;
         weno5_jp2(u, floor4, cen6, phim6, phip6);
-        lf_axis2(cen6, phim6, phip6, F2(inv_dx), F2(0.5f * alpha * inv_dx), pbar, diss);
+        lf_axis2(cen6, phim6, phip6, F2(inv_dx), hax, pbar, diss);
     } else {
         static_assert(SCHEME == ENO2 || SCHEME == ENO3, "paired ENO2, ENO3 or WENO5");
         F2 am, ap;
         if constexpr (SCHEME == ENO2) eno2_parts2(u, am, ap);
         else eno3_parts2(u, am, ap);
         pbar = (ap + am) * F2(0.5f * inv_dx);
-        diss = fma2(F2(0.5f * alpha * inv_dx), ap - am, diss);
+        diss = fma2(hax, ap - am, diss);
     }
 }
 
@@ -94,16 +95,21 @@ __device__ __forceinline__ void axis_pair(const F2* u, float floor4, float inv_d
 // faces (weno5_face2): one face evaluation per node instead of two one-sided
 // ones, the left-biased correction of the next plane carried in a register.
 // The results are bit-identical to FACES = false.  SCHEME: WENO5, ENO2 or
-// ENO3.  VARFORM: the rate of the variational form min[0, H] (Sec. VI-A,
-// Eq. 30), clipped at zero (for WENO5 the clip acts on 6 L, the same sign).
+// ENO3.  LOCAL (WENO5, state-only bounds): the stage's local-coefficient and
+// variational flags are honoured -- per-node dissipation coefficients
+// alpha_k(x) of each plane's node (LLF = LLLF for these bounds, Sec. IV-D)
+// and the rate of the variational form min[0, H] (Sec. VI-A, Eq. 30)
+// clipped at zero (the clip acts on 6 L, the same sign).
 template <int NDIM, int DYN, bool FACES = false, bool COH = false, int SCHEME = WENO5,
-          bool VARFORM = false>
+          bool LOCAL = false>
 __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int TB, int TA, int bx,
                                                 int by, int chunk, int outer, int ch, float* tile,
                                                 int tx, int ty)
 {
     static_assert(NDIM == 3 || NDIM == 4, "paired planes need a marching axis");
     static_assert(SCHEME == WENO5 || !FACES, "shared faces are a WENO5 form");
+    static_assert(!LOCAL || (SCHEME == WENO5 && DYN != QUADRATIC),
+                  "paired local coefficients: WENO5 with state-only bounds");
     constexpr int G = ghost_width(SCHEME);
     constexpr int AS = NDIM - 3, AA = NDIM - 2, AB = NDIM - 1;
     const int W = TB + 2 * G, H = TA + 2 * G, HW = H * W;
@@ -229,6 +235,33 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
         if (active) {
             const bool second = s + 1 < s_end;
             F2 u[2 * G + 1], pbar[NDIM], diss(0.f);
+            // alpha_k / (2 dx_k) of the two nodes: global, or (LOCAL with the
+            // stage's local flag) local to each node's state
+            F2 hx[NDIM];
+            if constexpr (LOCAL) {
+                x[AS] = F2(fmaf(float(s), a.h[AS], a.lo[AS]), fmaf(float(s + 1), a.h[AS], a.lo[AS]));
+                if (a.local_alpha) {
+                    float xa[NDIM], xb[NDIM];
+#pragma unroll
+                    for (int k = 0; k < NDIM; ++k) {
+                        xa[k] = x[k].x();
+                        xb[k] = x[k].y();
+                    }
+#pragma unroll
+                    for (int k = 0; k < NDIM; ++k)
+                        hx[k] = F2(local_alpha<DYN>(xa, k, a.prm, sth, cth, 0.f, 0.f) * (0.5f * a.inv_dx[k]),
+                                   local_alpha<DYN>(xb, k, a.prm, sth, cth, 0.f, 0.f) * (0.5f * a.inv_dx[k]));
+                } else {
+#pragma unroll
+                    for (int k = 0; k < NDIM; ++k) hx[k] = F2(0.5f * alpha[k] * a.inv_dx[k]);
+                }
+            }
+            // the global form forms its factor where it is used (not held in
+            // a live array across the loop)
+            auto hax = [&](int k) -> F2 {
+                if constexpr (LOCAL) return hx[k];
+                else return F2(0.5f * alpha[k] * a.inv_dx[k]);
+            };
             if constexpr (FACES) {
                 // faces s + 1/2 (x) and s + 3/2 (y): values w[1..6] and w[2..7]
                 F2 fm, cen, phip;
@@ -237,22 +270,21 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
                 weno5_face2(u, fl_s, fm, phip, cen);
                 const F2 phim(phim_next, fm.x());
                 phim_next = fm.y();
-                lf_axis2(cen, phim, phip, F2(a.inv_dx[AS]), F2(0.5f * alpha[AS] * a.inv_dx[AS]),
-                         pbar[AS], diss);
+                lf_axis2(cen, phim, phip, F2(a.inv_dx[AS]), hax(AS), pbar[AS], diss);
             } else {
 #pragma unroll
                 for (int o = 0; o <= 2 * G; ++o) u[o] = F2(w[o], w[o + 1]);
-                axis_pair<SCHEME>(u, fl_s, a.inv_dx[AS], alpha[AS], pbar[AS], diss);
+                axis_pair<SCHEME>(u, fl_s, a.inv_dx[AS], hax(AS), pbar[AS], diss);
             }
 #pragma unroll
             for (int o = 0; o <= 2 * G; ++o)
                 u[o] = F2(cur[(ty + o) * W + tx + G]);
-            axis_pair<SCHEME>(u, fl_a, a.inv_dx[AA], alpha[AA], pbar[AA], diss);
+            axis_pair<SCHEME>(u, fl_a, a.inv_dx[AA], hax(AA), pbar[AA], diss);
 #pragma unroll
             for (int o = 0; o <= 2 * G; ++o)
                 u[o] = F2(cur[(ty + G) * W + tx + o]);
             const F2 center = u[G];
-            axis_pair<SCHEME>(u, fl_b, a.inv_dx[AB], alpha[AB], pbar[AB], diss);
+            axis_pair<SCHEME>(u, fl_b, a.inv_dx[AB], hax(AB), pbar[AB], diss);
             if constexpr (NDIM == 4) {
                 const float* c0 = a.phi_s + s * sS + ia * sA + ib;
                 const float* c1 = c0 + (second ? sS : 0);
@@ -268,14 +300,15 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
                                       line_value<float, COH>(c1, outer + o, a.n[0], a.stride[0],
                                                  a.periodic[0]));
                 }
-                axis_pair<SCHEME>(u, weno_floor4(a.inv_dx[0]), a.inv_dx[0], alpha[0], pbar[0], diss);
+                axis_pair<SCHEME>(u, weno_floor4(a.inv_dx[0]), a.inv_dx[0], hax(0), pbar[0], diss);
             }
             x[AS] = F2(fmaf(float(s), a.h[AS], a.lo[AS]), fmaf(float(s + 1), a.h[AS], a.lo[AS]));
             F2 Hv = hamiltonian_pair<DYN, NDIM>(x, pbar, a.prm, sth, cth);  // kRate x H
             if constexpr (SCHEME == WENO5 && DYN == QUADRATIC)
                 Hv = Hv * F2(1.0f / 6.0f);  // 36 H -> 6 H
             F2 L = diss - Hv;
-            if constexpr (VARFORM) L = min2(L, F2(0.f));
+            if constexpr (LOCAL)
+                if (a.varform) L = min2(L, F2(0.f));
             const int idx = base_outer + s * sS + ia * sA + ib;
             F2 v = fma2(cs, center, clk * L);
             if (a.phi_n)
@@ -293,12 +326,12 @@ __device__ __forceinline__ void tiled_pair_body(const StageArgs<float>& a, int T
 
 // Single-problem launch of the paired body (FP32): blockDim = (tb, ta);
 // gridDim = (ceil(nB/tb), ceil(nA/ta), nchunks * nOuter).
-template <int NDIM, int DYN, int MINB, bool FACES, int SCHEME = WENO5, bool VARFORM = false>
+template <int NDIM, int DYN, int MINB, bool FACES, int SCHEME = WENO5, bool LOCAL = false>
 __global__ void __launch_bounds__(256, MINB) stage_pair_kernel(StageArgs<float> a, int ch, int nchunks)
 {
     extern __shared__ __align__(16) unsigned char smem_pair[];
     float* tile = reinterpret_cast<float*>(smem_pair);
-    tiled_pair_body<NDIM, DYN, FACES, false, SCHEME, VARFORM>(a, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y,
+    tiled_pair_body<NDIM, DYN, FACES, false, SCHEME, LOCAL>(a, blockDim.x, blockDim.y, blockIdx.x, blockIdx.y,
                                blockIdx.z % nchunks, blockIdx.z / nchunks, ch, tile, threadIdx.x,
                                threadIdx.y);
 }

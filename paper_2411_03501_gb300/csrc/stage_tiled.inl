@@ -16,11 +16,13 @@ static cudaError_t tiled_one(const StageArgs<float>& a, const Tile& t, cudaStrea
     dim3 grid((nB + t.tb - 1) / t.tb, (nA + t.ta - 1) / t.ta,
               nchunks * (NDIM == 4 ? a.n[0] : 1));
     const size_t smem = 2 * sizeof(float) * (t.ta + 2 * G) * (t.tb + 2 * G);
-    // (local coefficients never reach this file, nor the variational clip
-    // except on the WENO5 shared-face tile: launch_stage_tiled sends them to
-    // stage_tiled_local.cu; any other kernel here would drop the clip)
-    if (a.local_alpha || (a.varform && !(SCHEME == WENO5 && t.pair == 2)))
-        return cudaErrorInvalidValue;
+    // Local coefficients and the variational clip reach this file only on
+    // the WENO5 shared-face tile with state-only bounds (its local variant);
+    // launch_stage_tiled sends every other such stage to
+    // stage_tiled_local.cu, and any other kernel here would drop them.
+    constexpr bool kPairLocal = SCHEME == WENO5 && DYN != QUADRATIC;
+    const bool local = a.local_alpha || a.varform;
+    if (local && !(kPairLocal && t.pair == 2)) return cudaErrorInvalidValue;
     if constexpr (SCHEME == WENO5 || SCHEME == ENO2 || SCHEME == ENO3) {
         if (t.pair == 1) {
             stage_pair_kernel<NDIM, DYN, LSP_MINB, false, SCHEME><<<grid, block, 2 * smem, s>>>(a, t.ch, nchunks);
@@ -29,11 +31,14 @@ static cudaError_t tiled_one(const StageArgs<float>& a, const Tile& t, cudaStrea
     }
     if constexpr (SCHEME == WENO5) {
         if (t.pair == 2) {
-            if (a.varform)  // the variational form with global coefficients
-                stage_pair_kernel<NDIM, DYN, LSP_MINB, true, WENO5, true>
-                    <<<grid, block, 2 * smem, s>>>(a, t.ch, nchunks);
-            else
-                stage_pair_kernel<NDIM, DYN, LSP_MINB, true><<<grid, block, 2 * smem, s>>>(a, t.ch, nchunks);
+            if constexpr (kPairLocal) {
+                if (local) {
+                    stage_pair_kernel<NDIM, DYN, LSP_MINB, true, WENO5, true>
+                        <<<grid, block, 2 * smem, s>>>(a, t.ch, nchunks);
+                    return cudaGetLastError();
+                }
+            }
+            stage_pair_kernel<NDIM, DYN, LSP_MINB, true><<<grid, block, 2 * smem, s>>>(a, t.ch, nchunks);
             return cudaGetLastError();
         }
     }

@@ -1,8 +1,9 @@
 """Local dissipation coefficients (LLF, LLLF) and the variational form of the
 reachable-tube PDE on the GPU (through the C ABI) against the FP64 oracle:
 rates of every kernel family, steps and solves, the exact freezing of a
-receding front, the fallback of the paired WENO5 variants, batched solves,
-and the adjoint's refusal."""
+receding front, the paired WENO5 variants (the shared-face kernel's local
+variant, the plane-paired fallback), batched solves, and the adjoint's
+refusal."""
 import numpy as np
 import pytest
 import torch
@@ -32,7 +33,7 @@ def _spec(kind, scheme, dtype):
 
 CASES = [(k, s, d) for d in ("f32", "f64") for k, s in
          (("air3d", "weno5"), ("air3d", "eno3"), ("car4d", "eno3"), ("car4d", "eno2"),
-          ("quadratic3d", "weno5"), ("quadratic2d", "eno2"))]
+          ("car4d", "weno5"), ("quadratic3d", "weno5"), ("quadratic2d", "eno2"))]
 
 
 @pytest.mark.parametrize("diss,varform", [("llf", False), ("lllf", False), ("glf", True),
@@ -53,23 +54,47 @@ def test_rate_parity(kind, scheme, dtype, diss, varform):
         assert (got <= 0).all()
 
 
-@pytest.mark.parametrize("pair", [1, 2])
-def test_paired_tiles_fall_back_to_the_scalar_body(pair):
-    """The paired WENO5 variants evaluate the GLF form: with local
-    coefficients or the clip a paired tile runs the scalar body, giving the
-    scalar tile's bits."""
-    spec = _spec("air3d", "weno5", "f32")
-    spec.update(diss="llf", varform=True)
-    phi = rounded(W.smooth_field(spec, seed=3) + 0.2 * W.rough_field(spec, seed=4), "f32")
+def _rates_over_pairs(spec, phi, pairs):
     outs = []
-    for p in (0, pair):
+    for p in pairs:
         P = B.Problem(spec, check_finite=True)
         P.set_tile(16, 16, 7, 3, p)
         x = to_dev(phi, "f32")
         o = torch.empty_like(x)
         P.rate(x, o)
         outs.append(o)
+    return outs
+
+
+def test_plane_paired_tile_falls_back_to_the_scalar_body():
+    """The plane-paired WENO5 variant (pair = 1) evaluates the GLF form only:
+    with local coefficients or the clip the tile runs the scalar local body,
+    giving the scalar tile's bits."""
+    spec = _spec("air3d", "weno5", "f32")
+    spec.update(diss="llf", varform=True)
+    phi = rounded(W.smooth_field(spec, seed=3) + 0.2 * W.rough_field(spec, seed=4), "f32")
+    outs = _rates_over_pairs(spec, phi, (0, 1))
     assert torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("kind", ["air3d", "car4d"])
+@pytest.mark.parametrize("diss,varform", [("llf", False), ("lllf", True), ("glf", True)])
+def test_shared_face_local_variant_agrees_with_the_scalar_local_body(kind, diss, varform):
+    """The shared-face WENO5 kernel (pair = 2) has a local variant for
+    state-only bounds: per-node coefficients of each plane's state and the
+    clip.  It agrees with the scalar local body to FP32 rounding (the two
+    arrange the same WENO5 arithmetic differently): within the rate tolerance
+    of the oracle comparison, and both against the oracle."""
+    spec = _spec(kind, "weno5", "f32")
+    spec.update(diss=diss, varform=varform)
+    phi = rounded(W.smooth_field(spec, seed=3) + 0.2 * W.rough_field(spec, seed=4), "f32")
+    scalar, paired = (o.double().cpu().numpy() for o in _rates_over_pairs(spec, phi, (0, 2)))
+    want, alpha = oracle.rate(spec, phi)
+    tol = rate_tol(spec, phi, want, alpha)
+    compare(paired, scalar, tol, None, max_frac=0.0)
+    compare(paired, want, tol, None, max_frac=0.05)
+    if varform:
+        assert (paired <= 0).all()
 
 
 def test_receding_front_is_frozen_on_the_gpu():
