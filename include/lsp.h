@@ -228,7 +228,11 @@ lsp_status lsp_hj_solve(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
  * FP32 instructions, pair = 2 (WENO5 only) the same with the marching axis'
  * WENO5 terms evaluated once per face (shared by the two nodes of the face;
  * results identical to pair = 1 bit for bit).  A tile whose pair the scheme
- * has no variant for makes the step use the generic kernel.
+ * has no variant for makes the step use the generic kernel.  With local
+ * dissipation coefficients or the variational clip (opts->diss, varform),
+ * pair = 2 runs its local variant when the dynamics' bounds depend on the
+ * state only (every dynamics but QUADRATIC); other tiles run the scalar
+ * body with the local coefficients and the clip.
  *  lsp_set_tile(g, 0, 0, 0, 0, 0)   default: WENO5 16 x 16, 3 CTAs/SM, pair 2,
  *                                   chunks for ~3 waves (even length); other
  *                                   schemes 32 x 8, 3 CTAs/SM, chunks for ~2
