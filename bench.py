@@ -5,8 +5,11 @@ timed on the host cores beside it.
 
 One benchmark step = one complete reachable-tube solve of the workload
 (phi0 -> t_final: every RK stage of every step, CFL steps, tube), so the
-metric is  points * stages / time.  Default workload: the air3d game at
-201^3 (WENO5, RK3, CFL 0.75, t_final 2.8, FP32; 1747 steps, 5241 stages).
+metric is  points * stages / time.  Default workload: the 4-D car at 81^4
+(ENO3, RK3, CFL 0.75, t_final 1.0, FP32; 124 steps, 372 stages; 43 M nodes,
+fields of 172 MB), the largest configuration that fits one GPU; the air3d
+game at 201^3 (WENO5, RK3, t_final 2.8; 5241 stages) is measured first and
+reported inside the same line under "also".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...   # the FP64 oracle on the host cores
@@ -191,20 +194,35 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def sm_count() -> int:
+    """Streaming multiprocessors of the current device (152 on a GB300); 152
+    when no device is visible (the CPU tests of the accounting)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(torch.cuda.current_device())
+                       .multi_processor_count)
+    except Exception:
+        pass
+    return 152
+
+
 def roofline_of(flops: float, nbytes: float, seconds: float, traffic):
     """Roofline object of a kernel that does `flops` algorithmic FLOPs and
     moves `nbytes` algorithmic bytes per launch in `seconds`: the FP32 ALU
-    roof (152 SMs x 128 lanes x 2 x max SM clock) and the measured HBM copy
+    roof (SM count x 128 lanes x 2 x max SM clock) and the measured HBM copy
     roof; the binding one (larger fraction) first, the other inside."""
     peaks, src = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    nsm = sm_count()
+    alu_peak = nsm * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
     hbm_peak = float(peaks["hbm_gbs"])
     flop_ach = flops / seconds / 1e12
     hbm_ach = nbytes / seconds / 1e9
     alu = {"bound": "alu", "achieved": flop_ach, "peak": alu_peak, "unit": "TFLOP/s",
            "frac": flop_ach / alu_peak, "traffic": traffic,
-           "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x max SM clock"}
+           "peak_note": f"{nsm} SMs (queried) x 128 FP32 lanes x 2 (FMA) x max SM clock "
+                        f"({sm_mhz:.0f} MHz, {src})"}
     hbm = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
            "frac": hbm_ach / hbm_peak, "traffic": traffic,
            "peak_note": f"{src} STREAM copy"}
@@ -234,15 +252,27 @@ def run_reference(args, rank: int, world: int):
         return 0
     spec, phi0, g = workload_for(args)
     import numpy as np
+    import oracle
     npts = int(np.prod(spec["n"]))
+    # one benchmark step = one stage of the workload (a forward-Euler step
+    # from phi0 with the workload's first CFL step): npts updates
+    p0 = np.asarray(phi0, dtype=np.float64)
+    a = oracle.alpha(spec, p0)
+    dt = oracle.cfl_dt(spec, a, spec["cfl"], 0.0, spec["t_final"])
+    tgt = g if spec["tube"] else None
+
+    def one_stage():
+        t0 = time.perf_counter()
+        oracle.step(spec, p0, dt, 1, target=tgt)
+        return time.perf_counter() - t0
+
     for _ in range(args.warmup):
-        cpu_oracle_rate(spec, phi0, g, 1)
-    total, t_all, thr = 0.0, 0.0, 1
-    for _ in range(args.steps):
-        _, el, thr = cpu_oracle_rate(spec, phi0, g, 1)
-        t_all += el
-    v = npts * spec["rk"] * args.steps / t_all
-    sample = f"1 RK{spec['rk']} step ({spec['rk']} stages) of {spec['name']} from phi0 per benchmark step"
+        one_stage()
+    t_all = sum(one_stage() for _ in range(args.steps))
+    thr = oracle.threads()
+    v = npts * args.steps / t_all
+    sample = (f"1 stage (forward-Euler step, {npts} node updates) of {spec['name']} from phi0 "
+              f"per benchmark step, FP64, OpenMP over {thr} threads, {cpu_model()}")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
@@ -252,26 +282,27 @@ def run_reference(args, rank: int, world: int):
                    "parallelism": "single" if world == 1 else f"rank 0 alone of {world}",
                    "l2": "n/a (host)"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": cpu_model()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_ours(args, rank: int, world: int, local_rank: int):
+def measure_solve(args, name: str, rank: int, world: int, local_rank: int, clk_tag: str):
+    """One workload's measurement: K timed solves (device-resident inputs,
+    L2 flushed between solves), the pipelined end-to-end leg from pinned
+    host buffers and the roofline of the stage kernel.  Returns the fields of
+    its JSON line (rank 0) or None."""
     import numpy as np
     import torch
 
     from paper_2411_03501_gb300 import binding as B
-    from paper_2411_03501_gb300 import build as BLD
 
-    torch.cuda.set_device(local_rank)
-    if rank == 0 or not os.path.exists(BLD.LIB):
-        BLD.build()
-    if world > 1:
-        torch.distributed.barrier()
+    saved = args.workload
+    args.workload = name
     spec, phi0, g = workload_for(args)
+    args.workload = saved
     npts = int(np.prod(spec["n"]))
     P = B.Problem(spec, use_graph=args.graph)
     tdt = P.torch_dtype
@@ -305,7 +336,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     # flushed (and phi reset) between solves, outside the events
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    clk = ClockSampler(local_rank, os.path.join(args.outdir, f"clocks_rank{rank}.csv"))
+    clk = ClockSampler(local_rank, os.path.join(args.outdir, f"clocks_rank{rank}_{clk_tag}.csv"))
     barrier()
     with clk:
         for i in range(args.steps):
@@ -323,83 +354,173 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     units = world * npts * stages * args.steps
     value = units / (ms / 1e3)
 
-    # ---- end to end through the public API: pinned host inputs copied in,
-    # the solve, the result copied out, all inside the timed region
+    # ---- end to end through the public API: every step copies its inputs
+    # (phi0 and the target) from pinned host memory, solves, and copies the
+    # result back.  Two buffer sets and a copy stream: the copies of step
+    # i+1's inputs and of step i-1's result run while step i solves (a
+    # pipelined job of K solves); the timed region runs from the first
+    # upload to the last download.
     h_phi0 = torch.as_tensor(phi0).to(tdt).pin_memory()
     h_g = torch.as_tensor(g).to(tdt).pin_memory() if g is not None else None
-    h_out = torch.empty_like(h_phi0).pin_memory()
-    d_g = torch.empty_like(g_d) if g_d is not None else None
+    h_out = [torch.empty_like(h_phi0).pin_memory() for _ in range(2)]
+    d_phi = [torch.empty_like(phi0_d) for _ in range(2)]
+    d_g = [torch.empty_like(g_d) for _ in range(2)] if g_d is not None else [None, None]
     bi = h_phi0.numel() * h_phi0.element_size() + (h_g.numel() * h_g.element_size() if h_g is not None else 0)
-    bo = h_out.numel() * h_out.element_size()
-
-    def e2e_step():
-        phi.copy_(h_phi0, non_blocking=True)
-        if h_g is not None:
-            d_g.copy_(h_g, non_blocking=True)
-        P.solve(phi, d_g, 0.0, spec["t_final"])
-        h_out.copy_(phi, non_blocking=True)
-
-    if args.graph:
-        # the graph was captured for g_d; the e2e leg uses its own target buffer
-        P_e2e = B.Problem(spec, use_graph=True)
+    bo = h_out[0].numel() * h_out[0].element_size()
+    copy = torch.cuda.Stream()
+    P_e2e = P
+    if args.graph:  # the captured graph belongs to phi/g_d; the e2e leg has its own buffers
+        P_e2e = B.Problem(spec, use_graph=False)
         if tile[0] > 0:
             P_e2e.set_tile(*tile)
 
-        def e2e_step():  # noqa: F811
-            phi.copy_(h_phi0, non_blocking=True)
-            if h_g is not None:
-                d_g.copy_(h_g, non_blocking=True)
-            P_e2e.solve(phi, d_g, 0.0, spec["t_final"])
-            h_out.copy_(phi, non_blocking=True)
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
+    def e2e_run(K):
+        up = [torch.cuda.Event() for _ in range(2)]
+        done = [torch.cuda.Event() for _ in range(2)]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(copy)
+
+        def upload(i):
+            with torch.cuda.stream(copy):
+                d_phi[i % 2].copy_(h_phi0, non_blocking=True)
+                if h_g is not None:
+                    d_g[i % 2].copy_(h_g, non_blocking=True)
+                up[i % 2].record(copy)
+
+        upload(0)
+        for i in range(K):
+            stream.wait_event(up[i % 2])
+            P_e2e.solve(d_phi[i % 2], d_g[i % 2], 0.0, spec["t_final"], stream=stream)
+            done[i % 2].record(stream)
+            if i + 1 < K:
+                upload(i + 1)  # after step i-1's download on the copy stream
+            copy.wait_event(done[i % 2])
+            with torch.cuda.stream(copy):
+                h_out[i % 2].copy_(d_phi[i % 2], non_blocking=True)
+        e1.record(copy)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    e2e_run(max(2, args.warmup))
     barrier()
-    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.zero_()
-        ev2[i][0].record(stream)
-        e2e_step()
-        ev2[i][1].record(stream)
-    barrier()
-    ms2 = sum(a.elapsed_time(b) for a, b in ev2)
+    ms2 = e2e_run(args.steps)
     t2 = torch.tensor([ms2], dtype=torch.float64, device="cuda")
     if world > 1:
         torch.distributed.all_reduce(t2, op=torch.distributed.ReduceOp.MAX)
     e2e_value = units / (float(t2.item()) / 1e3)
-
+    # the same copies alone, to account for the e2e leg (not overlapped)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    d_phi[0].copy_(h_phi0, non_blocking=True)
+    if h_g is not None:
+        d_g[0].copy_(h_g, non_blocking=True)
+    h_out[0].copy_(d_phi[0], non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    copy_ms = c0.elapsed_time(c1)
     if rank != 0:
-        return 0
+        return None
 
     # ---- roofline of the dominant kernel (the fused stage kernel): its
     # average launch time over the timed region = solve time / stage launches
     per_launch_s = (ms / 1e3) / (stages * args.steps)
     bpn, fpn = algorithmic(spec)
     roof = roofline_of(fpn * npts, bpn * npts, per_launch_s, measured_traffic(spec["name"]))
-
-    # ---- the oracle on this host's cores: a bounded sample of the workload
-    cpu = None
-    if args.cpu_baseline:
-        v, el, thr = cpu_oracle_rate(spec, phi0, g, 1)
-        cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
-               "sample": f"1 RK{spec['rk']} step ({spec['rk']} stages, {el:.1f} s) of "
-                         f"{spec['name']} from phi0, FP64, OpenMP over {thr} threads"}
-
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": spec["dtype"], "data": "synthetic",
+    return {
+        "spec": spec, "phi0": phi0, "g": g, "value": value, "ms_per_step": ms / args.steps,
         "config": {"workload": spec["name"], "points": npts, "stages_per_step": stages,
-                   "rk_steps_per_step": stats["steps"], "parallelism": "replicas" if world > 1 else "single",
+                   "rk_steps_per_step": stats["steps"],
+                   "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed (512 MB write) between timed solves",
                    "graph": bool(args.graph), "tile": list(tile)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
-                "d2h_bytes_per_step": bo},
+                "d2h_bytes_per_step": bo,
+                "pipelined": "step i+1's uploads and step i-1's download overlap step i's solve "
+                             "(second stream, two buffer sets)",
+                "copy_ms_per_step_alone": copy_ms},
         "gpu_launches": stages * args.steps,
         "roofline": roof,
-        "cpu_baseline": cpu,
         "clocks": clk.summary(),
     }
+
+
+def cpu_model() -> str:
+    try:
+        for ln in subprocess.run(["lscpu"], capture_output=True, text=True).stdout.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline_of(spec, phi0, g):
+    """The FP64 oracle as it stands on this host: one RK step of the
+    workload on every core (OpenMP), and one stage (a forward-Euler step) on
+    one core over a slab of the grid (the first slices of the slowest axis,
+    same spacing, at least 7) so that it stays within seconds."""
+    import numpy as np
+    import oracle
+    v, el, thr = cpu_oracle_rate(spec, phi0, g, 1)
+    n0 = spec["n"][0]
+    k = max(7, n0 // 16) if spec["ndim"] >= 3 else n0
+    sub = dict(spec)
+    sub["n"] = [k] + list(spec["n"][1:])
+    h0 = (spec["hi"][0] - spec["lo"][0]) / ((n0) if spec["periodic"][0] else (n0 - 1))
+    sub["hi"] = [spec["lo"][0] + h0 * (k if spec["periodic"][0] else k - 1)] + list(spec["hi"][1:])
+    p = np.ascontiguousarray(np.asarray(phi0, dtype=np.float64)[:k])
+    gs = np.ascontiguousarray(np.asarray(g, dtype=np.float64)[:k]) if g is not None else None
+    a = oracle.alpha(spec, phi0)
+    dt = oracle.cfl_dt(spec, a, spec["cfl"], 0.0, spec["t_final"])
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.step(sub, p, dt, 1, target=gs if spec["tube"] else None)
+        el1 = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(thr)
+    v1 = int(np.prod(sub["n"])) / el1
+    return {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": f"1 RK{spec['rk']} step ({spec['rk']} stages, {el:.1f} s) of "
+                      f"{spec['name']} from phi0, FP64, OpenMP over {thr} threads",
+            "one_thread_value": v1,
+            "one_thread_sample": f"1 stage (forward-Euler step, {el1:.1f} s) on the first {k} "
+                                 f"slices of axis 0 ({int(np.prod(sub['n']))} nodes), 1 thread"}
+
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    from paper_2411_03501_gb300 import build as BLD
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0 or not os.path.exists(BLD.LIB):
+        BLD.build()
+    if world > 1:
+        torch.distributed.barrier()
+    also = [] if args.also in ("", "none") else args.also.split(",")
+    others = {}
+    for name in also:  # secondary workloads first; the headline line is measured last
+        r = measure_solve(args, name, rank, world, local_rank, name)
+        if r is not None:
+            others[r["config"]["workload"]] = {
+                "value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                "e2e": r["e2e"]["value"], "roofline": r["roofline"], "tile": r["config"]["tile"],
+                "stages_per_step": r["config"]["stages_per_step"], "clocks": r["clocks"]}
+    r = measure_solve(args, args.workload, rank, world, local_rank, "main")
+    if rank != 0:
+        return 0
+    spec = r["spec"]
+    cpu = cpu_baseline_of(spec, r["phi0"], r["g"]) if args.cpu_baseline else None
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": spec["dtype"], "data": "synthetic",
+        "config": r["config"], "e2e": r["e2e"], "gpu_launches": r["gpu_launches"],
+        "roofline": r["roofline"], "cpu_baseline": cpu, "clocks": r["clocks"],
+    }
+    if others:
+        line["also"] = others
     print(json.dumps(line), flush=True)
     return 0
 
@@ -813,7 +934,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="air3d_201")
+    ap.add_argument("--workload", default="car4d_81")
+    ap.add_argument("--also", default="auto",
+                    help="comma-separated solve workloads measured before the main one and "
+                         "reported inside its line (auto: air3d_201 with the default workload)")
     ap.add_argument("--graph", type=int, default=0)
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--outdir", default=os.path.join(ROOT, "bench_out"),
@@ -841,6 +965,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.also == "auto":
+        args.also = "air3d_201" if args.workload == "car4d_81" and args.mode == "solve" else ""
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if world > 1:

@@ -227,7 +227,17 @@ lsp_status lsp_hj_solve(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
  * the variant that carries two consecutive planes per thread through paired
  * FP32 instructions, pair = 2 (WENO5 only) the same with the marching axis'
  * WENO5 terms evaluated once per face (shared by the two nodes of the face;
- * results identical to pair = 1 bit for bit).  A tile whose pair the scheme
+ * results identical to pair = 1 bit for bit).  pair = 3 (ENO2 and ENO3)
+ * selects the face-shared ENO kernel: each thread owns 4 consecutive nodes
+ * of the fastest axis, so a CTA has tb/4 x ta threads and tb is 16, 28 or
+ * 32; every ENO stencil choice is made once per cell face for both nodes of
+ * the face (along the fastest axis within a thread's run, along the
+ * marching axis in a register pipeline); minb is 2 (128 registers) for it.
+ * pair = 4 is the same with runs of 2 nodes (tb/2 x ta threads, minb 3: 80
+ * registers, more resident warps).
+ * Its results agree with the other variants to FP32 rounding, not bit for
+ * bit (the same selections, the arithmetic grouped differently).  A tile
+ * whose pair the scheme
  * has no variant for makes the step use the generic kernel.  With local
  * dissipation coefficients or the variational clip (opts->diss, varform),
  * pair = 2 runs its local variant when the dynamics' bounds depend on the
@@ -239,8 +249,11 @@ lsp_status lsp_hj_solve(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
  *                                   waves
  *  lsp_set_tile(g, -1, 0, 0, 0, 0)  always use the generic kernel
  *  lsp_set_tile(g, tb, ta, ch, minb, pair) explicit; LSP_EINVAL unless
- *        tb*ta <= 256, the haloed tile fits 3 values per thread, the launch
- *        has <= 65535 z-blocks, minb is 2, 3 or 4 and pair is 0, 1 or 2.
+ *        the launch has <= 65535 z-blocks, minb is 2, 3 or 4 and either
+ *        pair is 0, 1 or 2 with tb*ta <= 256 and the haloed tile fitting 3
+ *        values per thread, or pair is 3 (4) with tb in {16, 28, 32},
+ *        (tb/4)*ta <= 256 ((tb/2)*ta <= 256) and two staged planes within
+ *        200 KB of shared memory.
  * lsp_get_tile reports the tile a step with `opts` would use (all -1 when
  * the generic kernel runs). */
 lsp_status lsp_set_tile(lsp_grid* grid, int tb, int ta, int ch, int minb, int pair);
@@ -252,7 +265,8 @@ lsp_status lsp_get_tile(const lsp_grid* grid, const lsp_solve_opts* opts, int* t
  * fields are allocated for the call, and without room for them the first
  * stage alone is timed) for a set of tile shapes (7 fixed, 2 fitted to the
  * grid), chunk lengths, occupancy targets and kernel variants (WENO5: pair 0,
- * 1, 2; ENO2 and ENO3: pair 0, 1; up to 9 x 7 x 3 x 3 candidates), re-time the
+ * 1, 2; ENO2 and ENO3: pair 0, 1, plus the face-shared runs of pairs 3 and
+ * 4 on 3 widths x 4 row counts x 7 chunk lengths), re-time the
  * six fastest over longer windows and keep the best in the grid handle
  * (reported through tb/ta/ch/minb/pair, which may be NULL).  Waits for the
  * GPU.  For grids without a tiled kernel it selects the generic one (all
@@ -273,13 +287,18 @@ lsp_status lsp_autotune(lsp_grid* grid, const lsp_solve_opts* opts, const void* 
  *    whose lsp_workspace_size exceeds 32 MiB are rejected with LSP_ENOMEM
  *    and a message giving both sizes (FP32 RK3: up to ~4.19M nodes).
  *  - The first call on a device looks up the array's device address (a
- *    one-time set-up with that device current); make that first call before
- *    any stream capture.
- *  - Every call shares the one array, which keeps the last call's contents
- *    (the solve never reads them: flags are cleared on entry and stage
- *    fields are written before being read).  Calls whose GPU work overlaps
- *    (different streams, threads or processes on the same device) race on
- *    it: serialise them.
+ *    one-time set-up with that device current) and keeps it for the life of
+ *    the process; make that first call before any stream capture.  Because
+ *    the address is kept per device index, resetting the device
+ *    (cudaDeviceReset) or making a non-primary context current on it after
+ *    that first call is not supported: the module is then loaded again at
+ *    another address and the kept one is stale.
+ *  - Every call in a process shares the one array, which keeps the last
+ *    call's contents (the solve never reads them: flags are cleared on entry
+ *    and stage fields are written before being read).  Calls in one process
+ *    whose GPU work overlaps (different streams or host threads) race on it:
+ *    serialise them.  Separate processes each have their own copy of the
+ *    array (one per CUDA context) and do not interfere.
  *  - opts->use_graph must be 0.  Other arguments, results and errors as for
  *    lsp_hj_solve.  Nothing is allocated. */
 lsp_status lsp_hj_solve_noalloc(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,

@@ -126,6 +126,8 @@ def lib():
         L.orc_adjoint.restype = ctypes.c_int
         L.orc_threads.argtypes = []
         L.orc_threads.restype = ctypes.c_int
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_set_threads.restype = None
         _lib = L
     return _lib
 
@@ -133,6 +135,11 @@ def lib():
 def threads() -> int:
     """OpenMP threads the oracle uses (1 if built without OpenMP)."""
     return int(lib().orc_threads())
+
+
+def set_threads(n: int) -> None:
+    """Use n OpenMP threads in later calls (for timing on one core)."""
+    lib().orc_set_threads(int(n))
 
 
 def _problem(spec: dict) -> _Problem:

@@ -757,6 +757,17 @@ int orc_threads(void)
 #endif
 }
 
+/* Set the number of OpenMP threads of later calls (no effect without
+ * OpenMP); used to time the oracle on one core and on all cores. */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Point evaluations, exported for the tests that pin the closed forms:
  * the Hamiltonian at one state/costate, and the per-node bound on |dH/dp_k|. */
 double orc_ham(const orc_problem* P, const double* x, const double* p)

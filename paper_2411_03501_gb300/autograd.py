@@ -5,7 +5,9 @@ library).
 ``HJTube(spec, nsteps)`` holds a grid and a workspace; ``tube(phi0, target,
 params)`` returns phi after ``nsteps`` fixed CFL steps and is differentiable
 with respect to phi0, the target and the dynamics parameters (the reverse
-sweep of ``lsp_hj_adjoint`` with sqrt(N) checkpoints).  ``tube.loss(phi,
+sweep of ``lsp_hj_adjoint`` with sqrt(N) checkpoints).  The checkpoints live
+in the tube's workspace, so only the latest forward of a tube can be
+differentiated: a backward through an earlier one raises.  ``tube.loss(phi,
 queries)`` is the smoothed tube volume plus the values at query states,
 differentiable with respect to phi.
 """
@@ -24,6 +26,10 @@ class _SolveFn(torch.autograd.Function):
         tgt = target.detach().contiguous() if target is not None else None
         B.lsp_hj_solve_ckpt(tube.grid, tube.opts, phi, tgt, tube.nsteps, tube.ncheck,
                             tube.workspace)
+        # the checkpoints of this forward live in the tube's workspace until
+        # the next forward on the same tube overwrites them
+        tube._generation += 1
+        ctx.generation = tube._generation
         ctx.tube = tube
         ctx.params = params.detach().clone()
         ctx.save_for_backward(tgt if tgt is not None else torch.empty(0))
@@ -33,6 +39,11 @@ class _SolveFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_phi):
         tube = ctx.tube
+        if tube._generation != ctx.generation:
+            raise RuntimeError(
+                "HJTube: the workspace holding this forward's checkpoints was reused by a later "
+                "forward on the same tube; call backward before the next forward, or use one "
+                "HJTube per live graph")
         (tgt,) = ctx.saved_tensors
         tgt = tgt if ctx.has_target else None
         tube._set_params(ctx.params)  # the sweep needs the forward's dynamics
@@ -73,6 +84,7 @@ class HJTube:
         self.grid = B.lsp_grid_create(d, spec["lo"], spec["hi"], spec["n"],
                                       ["periodic" if p else "extrapolate" for p in spec["periodic"]])
         self._params = None
+        self._generation = 0  # forwards run so far (checkpoints belong to the last one)
         self._set_params(torch.tensor(spec["params"], dtype=torch.float64))
         self.opts = B.make_opts(spec.get("rk", 3), spec["scheme"], spec.get("dtype", "f32"),
                                 spec.get("tube", False), spec.get("cfl", 0.75))

@@ -211,7 +211,7 @@ __device__ __forceinline__ void ham_grad(const R* x, const R* p, const R* prm, R
         R n2 = R(0);
 #pragma unroll
         for (int k = 0; k < NDIM; ++k) n2 += p[k] * p[k];
-        const R n = rsqrt_(n2);
+        const R n = real_sqrt(n2);
 #pragma unroll
         for (int k = 0; k < NDIM; ++k) hp[k] = n > R(0) ? prm[0] * p[k] / n : R(0);
         hprm[0] = n;

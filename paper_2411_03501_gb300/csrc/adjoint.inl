@@ -9,7 +9,7 @@ namespace lsp {
 static inline int adj_blocks(long long npts)
 {
     long long b = (npts + 255) / 256;
-    const long long cap = 152LL * 16;
+    const long long cap = 16LL * sm_count();
     return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
@@ -21,9 +21,7 @@ template <int NDIM, int SCHEME, int DYN>
 static cudaError_t launch_pass_a(const AdjArgs<LSP_REAL>& a, cudaStream_t s)
 {
     static const int resident = [] {
-        int dev = 0, nsm = 152, per = 1;
-        if (cudaGetDevice(&dev) == cudaSuccess)
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        int nsm = sm_count(), per = 1;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                 &per, adj_stage_a<NDIM, SCHEME, DYN, LSP_REAL>, 256, 0) != cudaSuccess || per < 1)
             per = 1;

@@ -8,7 +8,7 @@ namespace lsp {
 static inline int stage_blocks(long long npts)
 {
     long long b = (npts + 255) / 256;
-    const long long cap = 152LL * 16;  // grid-stride beyond 16 blocks per SM
+    const long long cap = 16LL * sm_count();  // grid-stride beyond 16 blocks per SM
     return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 

@@ -28,6 +28,14 @@ cudaError_t launch_stage_tiled_m(int ndim, int scheme, int dyn, const StageArgs<
 cudaError_t launch_stage_tiled(int ndim, int scheme, int dyn, const StageArgs<float>& a,
                                const Tile& t, cudaStream_t s);
 bool tile_valid(int ndim, int scheme, const Tile& t, const int* n);
+// Face-shared ENO2/ENO3 kernel with R-node runs per thread (stage_run.cuh):
+// Tile.pair = 3 runs of 4 (stage_run_r4.cu), 4 runs of 2 (stage_run_r2.cu);
+// tb = nodes of the fastest axis per CTA (16, 28 or 32).
+constexpr size_t kRunMaxSmem = 200 * 1024;  // dynamic shared memory of a launch
+template <int R>
+cudaError_t launch_stage_run_r(int ndim, int scheme, int dyn, const StageArgs<float>& a,
+                               const Tile& t, cudaStream_t s);
+bool run_tile_ok(int ndim, int scheme, int run, int tb, int ta);
 // The same stage with local coefficients / the variational clip compiled in
 // (stage_tiled_local.cu); launch_stage_tiled routes there when a asks for them.
 cudaError_t launch_stage_tiled_local(int ndim, int scheme, int dyn, const StageArgs<float>& a,

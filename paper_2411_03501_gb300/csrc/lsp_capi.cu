@@ -144,7 +144,7 @@ lsp::Tile default_tile(const lsp_grid* g, int scheme)
     t.pair = paired ? 2 : 0;
     const long long nplane = (long long)((g->n[d - 1] + t.tb - 1) / t.tb) *
                              ((g->n[d - 2] + t.ta - 1) / t.ta) * (d == 4 ? g->n[0] : 1);
-    const long long want = paired ? 3LL * 3 * 152 : 2LL * 2 * 152;
+    const long long want = (paired ? 3LL * 3 : 2LL * 2) * lsp::sm_count();
     long long nch = (want + nplane - 1) / nplane;
     const int nS = g->n[d - 3];
     if (nch > nS / 4) nch = nS / 4;
@@ -662,7 +662,9 @@ lsp_status lsp_set_tile(lsp_grid* g, int tb, int ta, int ch, int minb, int pair)
         return LSP_OK;
     }
     lsp::Tile t{tb, ta, ch, minb, pair};
-    if (!lsp::tile_valid(g->ndim, LSP_WENO5, t, g->n))
+    // validated for a scheme that has the variant (the step re-checks the
+    // tile against its own scheme and runs the generic kernel if it fails)
+    if (!lsp::tile_valid(g->ndim, pair >= 3 ? LSP_ENO3 : LSP_WENO5, t, g->n))
         return fail(LSP_EINVAL, "tile %dx%dx%d (%d CTAs/SM) is not valid for this grid", tb, ta,
                     ch, minb);
     g->tile = t;
@@ -772,16 +774,40 @@ lsp_status lsp_autotune(lsp_grid* g, const lsp_solve_opts* o, const void* phi, v
         return enqueue_stage<float>(&trial, o, ctl, (const float*)phi, nullptr, nullptr, w1, dt,
                                     0.0, 1.0, 1.0, false, st);
     };
-    for (int si = 0; si < nshapes; ++si) {
-        const int* sh = shapes[si];
+    // the face-shared ENO runs (pair 3: 4 nodes per thread, pair 4: 2): 16,
+    // 28 or 32 nodes of the fastest axis per CTA and 4, 8 or 16 rows, or as
+    // many rows as split the second-fastest axis evenly into tiles of at most
+    // 16
+    int run_rows[4] = {4, 8, 16, 0};
+    {
+        const int nA = g->n[d - 2];
+        const int k = (nA + 15) / 16;
+        run_rows[3] = (nA + k - 1) / k;
+    }
+    const bool eno = o->scheme == LSP_ENO2 || o->scheme == LSP_ENO3;
+    const int nrun = eno ? 3 * 4 : 0;
+    for (int si = 0; si < nshapes + nrun; ++si) {
+        const bool run = si >= nshapes;
+        const int run_tb[3] = {16, 28, 32};
+        const int sh[2] = {run ? run_tb[(si - nshapes) / 4] : shapes[si][0],
+                           run ? run_rows[(si - nshapes) % 4] : shapes[si][1]};
+        if (run && (si - nshapes) % 4 == 3) {
+            bool dup = false;
+            for (int q = 0; q < 3; ++q) dup |= run_rows[q] == sh[1];
+            if (dup) continue;
+        }
         for (int cand = 0; cand < 63; ++cand) {
             const int sp = splits[cand % 7];
             const int minb = 2 + (cand / 7) % 3;
-            const int pair = cand / 21;
+            int pair = cand / 21;
+            if (run) {  // runs of 4 (128 registers) and of 2 (80 registers)
+                if (cand >= 14) break;
+                pair = cand < 7 ? 3 : 4;
+            }
             if (pair == 2 && o->scheme != LSP_WENO5) continue;
             if (pair == 1 && o->scheme == LSP_UPWIND1) continue;
             const int nS = g->n[d - 3];
-            lsp::Tile t{sh[0], sh[1], (nS + sp - 1) / sp, minb, pair};
+            lsp::Tile t{sh[0], sh[1], (nS + sp - 1) / sp, run ? (pair == 3 ? 2 : 3) : minb, pair};
             if (!lsp::tile_valid(d, o->scheme, t, g->n)) continue;
             trial.tile = t;
             trial.tile_mode = 1;

@@ -15,6 +15,22 @@ enum Dyn { NORMAL_SPEED = 0, TRANSLATE = 1, QUADRATIC = 2, AIR3D = 3, CAR4D = 4,
 
 __host__ __device__ constexpr int ghost_width(int scheme) { return scheme == UPWIND1 ? 1 : (scheme == ENO2 ? 2 : 3); }
 
+// Streaming multiprocessors of the current device, queried once per device
+// index (152 on a GB300), for sizing grids in waves of resident CTAs.
+inline int sm_count()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 1;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 // Device control block, the first 256 bytes of every workspace.
 struct Ctl {
     unsigned long long alpha_bits[LSP_MAXD];  // p-dependent GLF alpha (bits of

@@ -58,6 +58,9 @@ extern "C" lsp_status lsp_hj_solve_noalloc(lsp_grid* grid, const lsp_solve_opts*
     {
         // Set-up, once per device with that device current: the device
         // address of the static array (the host-side symbol is not one).
+        // Kept per device index for the life of the process; after a
+        // cudaDeviceReset the module would load at another address, which
+        // is why resetting the device after the first call is unsupported.
         std::lock_guard<std::mutex> lock(g_scratch_mu);
         if (!g_scratch_ptr[dev]) {
             void* p = nullptr;

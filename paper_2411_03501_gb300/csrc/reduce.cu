@@ -11,7 +11,8 @@ namespace lsp {
 cudaError_t launch_alpha_state(int dyn, const GridGeom& g, unsigned long long* out, cudaStream_t s)
 {
     long long b = (g.npts + 255) / 256;
-    const int nb = (int)(b < 152 * 8 ? (b < 1 ? 1 : b) : 152 * 8);
+    const long long cap = 8LL * sm_count();
+    const int nb = (int)(b < cap ? (b < 1 ? 1 : b) : cap);
     switch (dyn) {
     case NORMAL_SPEED: alpha_state_kernel<NORMAL_SPEED><<<nb, 256, 0, s>>>(g, out); break;
     case TRANSLATE: alpha_state_kernel<TRANSLATE><<<nb, 256, 0, s>>>(g, out); break;
@@ -28,8 +29,15 @@ bool tile_valid(int ndim, int scheme, const Tile& t, const int* n)
 {
     if (ndim != 3 && ndim != 4) return false;
     const int G = ghost_width(scheme);
-    if (t.tb < 1 || t.ta < 1 || t.ch < 1 || t.tb * t.ta > 256) return false;
+    if (t.tb < 1 || t.ta < 1 || t.ch < 1) return false;
     if (t.minb < 2 || t.minb > 4) return false;
+    const int nS = n[ndim - 3];
+    const long long nz = (long long)((nS + t.ch - 1) / t.ch) * (ndim == 4 ? n[0] : 1);
+    if (t.pair == 3 || t.pair == 4) {  // face-shared ENO runs of 4 or 2 nodes
+        return (scheme == ENO2 || scheme == ENO3) &&
+               run_tile_ok(ndim, scheme, t.pair == 3 ? 4 : 2, t.tb, t.ta) && nz <= 65535;
+    }
+    if (t.tb * t.ta > 256) return false;
     // pair 1: paired planes (WENO5, ENO2, ENO3); pair 2: WENO5 shared faces
     if (t.pair < 0 || t.pair > 2) return false;
     if (t.pair == 1 && scheme != WENO5 && scheme != ENO2 && scheme != ENO3) return false;
@@ -37,9 +45,16 @@ bool tile_valid(int ndim, int scheme, const Tile& t, const int* n)
     // each thread stages at most 3 values of the haloed plane tile (MAXE of
     // the tiled bodies; every shape the autotuner tries qualifies)
     if ((t.ta + 2 * G) * (t.tb + 2 * G) > 3 * t.ta * t.tb) return false;
-    const int nS = n[ndim - 3];
-    const long long nz = (long long)((nS + t.ch - 1) / t.ch) * (ndim == 4 ? n[0] : 1);
     return nz <= 65535;
+}
+
+bool run_tile_ok(int ndim, int scheme, int run, int tb, int ta)
+{
+    if (tb != 16 && tb != 28 && tb != 32) return false;
+    const int tbt = tb / run, G = ghost_width(scheme);
+    const size_t floats = (size_t)(ta + 2 * G) * (tb + 8) +
+                          (size_t)((ndim == 4 ? 2 * G : 0) + 3) * ta * tb;
+    return ta >= 1 && tbt * ta <= 256 && 2 * sizeof(float) * floats <= kRunMaxSmem;
 }
 
 cudaError_t launch_stage_tiled(int ndim, int scheme, int dyn, const StageArgs<float>& a,
@@ -48,8 +63,14 @@ cudaError_t launch_stage_tiled(int ndim, int scheme, int dyn, const StageArgs<fl
     // local coefficients and the variational clip run the scalar local
     // bodies, except on the WENO5 shared-face tile with state-only bounds,
     // whose kernel has a local variant
-    if ((a.local_alpha || a.varform) && !(scheme == WENO5 && t.pair == 2 && dyn != QUADRATIC))
-        return launch_stage_tiled_local(ndim, scheme, dyn, a, t, s);
+    if ((a.local_alpha || a.varform) && !(scheme == WENO5 && t.pair == 2 && dyn != QUADRATIC)) {
+        // the face-shared runs have no local variant: a one-node-per-thread
+        // tile of the same chunking runs the local body
+        const Tile tl = t.pair >= 3 ? Tile{32, 8, t.ch, 3, 0} : t;
+        return launch_stage_tiled_local(ndim, scheme, dyn, a, tl, s);
+    }
+    if (t.pair == 3) return launch_stage_run_r<4>(ndim, scheme, dyn, a, t, s);
+    if (t.pair == 4) return launch_stage_run_r<2>(ndim, scheme, dyn, a, t, s);
     switch (t.minb) {
     case 2: return launch_stage_tiled_m<2>(ndim, scheme, dyn, a, t, s);
     case 3: return launch_stage_tiled_m<3>(ndim, scheme, dyn, a, t, s);
@@ -62,7 +83,8 @@ cudaError_t launch_alpha_argmax(int dyn, const GridGeom& g, const double* alpha,
                                 unsigned long long* out, cudaStream_t s)
 {
     long long b = (g.npts + 255) / 256;
-    const int nb = (int)(b < 152 * 8 ? (b < 1 ? 1 : b) : 152 * 8);
+    const long long cap = 8LL * sm_count();
+    const int nb = (int)(b < cap ? (b < 1 ? 1 : b) : cap);
     switch (dyn) {
     case NORMAL_SPEED: alpha_argmax_kernel<NORMAL_SPEED><<<nb, 256, 0, s>>>(g, alpha, out); break;
     case TRANSLATE: alpha_argmax_kernel<TRANSLATE><<<nb, 256, 0, s>>>(g, alpha, out); break;

@@ -52,7 +52,7 @@ __device__ __forceinline__ R shape_value(const ShapeDev<R>& s, const R* x)
 #pragma unroll
         for (int k = 0; k < NDIM; ++k)
             if (!((s.ignore >> k) & 1u)) q += (x[k] - s.c[k]) * (x[k] - s.c[k]);
-        return rsqrt_(q) - s.r;
+        return real_sqrt(q) - s.r;
     }
     if (s.kind == SHAPE_BOX) {  // exact signed distance to [c, d]
         R out2 = R(0), in = R(-INFINITY);
@@ -63,7 +63,7 @@ __device__ __forceinline__ R shape_value(const ShapeDev<R>& s, const R* x)
             if (e > R(0)) out2 += e * e;
             in = rmax(in, e);
         }
-        return out2 > R(0) ? rsqrt_(out2) : in;
+        return out2 > R(0) ? real_sqrt(out2) : in;
     }
     if (s.kind == SHAPE_QUADRIC) {  // sum_k w_k (x_k - c_k)^2 - offset
         R q = R(0);
@@ -80,7 +80,7 @@ __device__ __forceinline__ R shape_value(const ShapeDev<R>& s, const R* x)
             q += s.d[k] * (x[k] - s.c[k]);
             nn += s.d[k] * s.d[k];
         }
-    return q / rsqrt_(nn);
+    return q / real_sqrt(nn);
 }
 
 // The coordinates of node i: its index split by the axis lengths (the
@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(256) shape_op_kernel(int op, const R* a, const
 static int shape_blocks(long long n)
 {
     const long long b = (n + 255) / 256;
-    return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+    const long long cap = 16LL * sm_count();
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 template <typename R>

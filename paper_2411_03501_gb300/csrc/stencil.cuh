@@ -42,8 +42,8 @@ __device__ __forceinline__ float rmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double rmax(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float rmin(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double rmin(double a, double b) { return fmin(a, b); }
-__device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
-__device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float real_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double real_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ void rsincos(float x, float* s, float* c) { sincosf(x, s, c); }
 __device__ __forceinline__ void rsincos(double x, double* s, double* c) { sincos(x, s, c); }
 
@@ -182,7 +182,7 @@ __device__ __forceinline__ R hamiltonian(const R* x, const R* p, const R* prm)
         R s = R(0);
 #pragma unroll
         for (int k = 0; k < NDIM; ++k) s += p[k] * p[k];
-        return prm[0] * rsqrt_(s);
+        return prm[0] * real_sqrt(s);
     } else if constexpr (DYN == TRANSLATE) {
         R s = R(0);
 #pragma unroll

@@ -15,6 +15,13 @@ def pytest_configure(config):
 
 @pytest.fixture(scope="session")
 def orc():
+    path = os.environ.get("LSP_ORACLE_PY")
+    if path:  # a copy of the oracle's Python layer with a planted mistake
+        import importlib.util
+        spec = importlib.util.spec_from_file_location("oracle_mutant", path)
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+        return mod
     import oracle
     oracle.build()
     return oracle

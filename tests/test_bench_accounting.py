@@ -44,7 +44,7 @@ def test_algorithmic_flops_of_the_benchmark_stages():
 
 def test_roofline_object_picks_the_binding_roof():
     peaks, _ = bench._peaks()
-    alu_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    alu_peak = bench.sm_count() * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     # compute-heavy: 505 FLOP and 12 B per node, 8.12 M nodes in 126 us
     n = 8120601
     r = bench.roofline_of(505.0 * n, 12.0 * n, 126e-6, 68.7e6)

@@ -196,3 +196,77 @@ def test_adjoint_workload_fp32_against_fd_and_fp64():
     np.testing.assert_allclose(res["f64"], fd["f64"], rtol=1e-5, atol=1e-6)
     np.testing.assert_allclose(res["f32"], res["f64"], rtol=2e-2, atol=1e-3)
     np.testing.assert_allclose(res["f32"], fd["f32"], rtol=6e-2, atol=1e-2)
+
+
+def _seam_and_edge_queries(spec, rng, nq):
+    """Seeded query states uniform over the domain, plus states across the
+    periodic theta seam (just below 2 pi, above it, below 0) and beyond the
+    clamped x and y edges."""
+    q = np.stack([rng.uniform(spec["lo"][k], spec["hi"][k], nq) for k in range(3)], 1)
+    dth = 2 * np.pi / spec["n"][2]
+    extra = np.array([[3.3, -1.7, 2 * np.pi - dth / 2], [0.4, 2.2, 2 * np.pi + dth / 4],
+                      [-2.0, 5.0, -dth / 3], [25.0, 1.0, 0.4], [-8.0, -12.0, 5.0],
+                      [4.0, 12.5, 2 * np.pi - 1e-3]])
+    return np.concatenate([q, extra], 0)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_device_loss_matches_oracle(dtype):
+    """lsp_loss_tube (smoothed volume of {phi <= 0} plus multilinear values at
+    query states) against oracle.loss and oracle.loss_grad, value and
+    gradient field element by element, with queries across the periodic
+    theta seam and beyond the clamped edges.  The value is accumulated in
+    FP64 from the field's values and the query coordinates as stored (the
+    oracle gets the same rounded inputs), so it agrees to FP64 rounding in
+    both precisions; the FP32 gradient is the volume term rounded to FP32
+    plus the query weights added by FP32 atomics (a few u relative, u = 2^-24,
+    plus u per unit weight)."""
+    spec = W.air3d(nx=[33, 29, 31], dtype=dtype)[0]
+    rng = np.random.default_rng(20241106)
+    phi = rounded(W.circle_sdf(spec, 4.0, center=[7.0, 0.5]) + 0.3 * W.smooth_field(spec, seed=2),
+                  dtype)
+    q = rounded(_seam_and_edge_queries(spec, rng, 64), dtype)
+    P = B.Problem(spec)
+    val = torch.zeros(1, dtype=torch.float64, device="cuda")
+    grad = torch.empty(spec["n"], dtype=torch.float64 if dtype == "f64" else torch.float32,
+                       device="cuda")
+    B.lsp_loss_tube(P.grid, dtype, to_dev(phi, dtype), to_dev(q, dtype), val, grad)
+    torch.cuda.synchronize()
+    want = oracle.loss(spec, phi, q)
+    want_g = oracle.loss_grad(spec, phi, q)
+    got_g = grad.double().cpu().numpy()
+    if dtype == "f64":
+        assert abs(val.item() - want) <= 1e-12 * abs(want)
+        np.testing.assert_allclose(got_g, want_g, rtol=1e-12, atol=1e-15)
+    else:
+        assert abs(val.item() - want) <= 1e-10 * abs(want), (val.item(), want)
+        tol_g = 8 * 2.0 ** -24 * (np.abs(want_g) + 1.0)
+        assert np.all(np.abs(got_g - want_g) <= tol_g), np.abs(got_g - want_g).max()
+
+
+def test_backward_through_an_overwritten_forward_raises():
+    """Two forwards on one tube, then the backward of the first: its
+    checkpoints were overwritten by the second forward, so the backward
+    raises instead of returning another forward's gradients; the backward of
+    the second forward equals that of a tube used once."""
+    spec, sdf, q = _air3d_adjoint_problem(17, 6, "f64")
+    sdf_t = torch.as_tensor(sdf, device="cuda")
+    q_t = torch.as_tensor(q, device="cuda")
+
+    def grads(tube, r0):
+        params = torch.tensor(spec["params"], dtype=torch.float64, requires_grad=True)
+        r = torch.tensor(r0, dtype=torch.float64, device="cuda", requires_grad=True)
+        return _loss_of(tube, sdf_t, q_t, r, params), params
+
+    tube = HJTube(spec, nsteps=6)
+    L1, p1 = grads(tube, 5.0)
+    L2, p2 = grads(tube, 4.5)
+    with pytest.raises(RuntimeError, match="reused by a later forward"):
+        L1.backward()
+    L2.backward()
+    fresh = HJTube(spec, nsteps=6)
+    L3, p3 = grads(fresh, 4.5)
+    L3.backward()
+    # the same computation up to the order of FP64 atomic accumulations
+    assert L2.item() == pytest.approx(L3.item(), rel=1e-12)
+    torch.testing.assert_close(p2.grad, p3.grad, rtol=1e-10, atol=1e-12)

@@ -51,9 +51,10 @@ def test_batched_equals_single_problem_solves(use_graph):
 def test_batched_matches_oracle_on_small_problems():
     """A few batched problems against the FP64 oracle's own solves, with the
     FP32 precision bar of the single-problem tests (check_fp32_solve: 1e-4
-    max|phi|, or 3x the oracle's own spread under FP32-sized noise where the
-    discrete problem is worse conditioned -- e.g. the symmetric valley at
-    theta = 0, y = 0 of an air3d tube, which FP32 rounding desymmetrises)."""
+    max|phi| at every node except the few where the oracle itself, perturbed
+    by FP32-sized noise, moves by more than a third of that -- e.g. the
+    symmetric valley at theta = 0, y = 0 of an air3d tube, which FP32
+    rounding desymmetrises -- and 3x the oracle's own response there)."""
     specs, phis, gs = _mixed(scale=0.3, count=6, seed=7)
     Bt = B.Batch(specs)
     xs = [to_dev(p, "f32") for p in phis]
@@ -62,8 +63,8 @@ def test_batched_matches_oracle_on_small_problems():
     for i, sp in enumerate(specs):
         want, _ = oracle.solve(sp, phis[i], sp["t_final"], sp["rk"], sp["cfl"], target=gs[i])
         got = xs[i].double().cpu().numpy()
-        spread = noise_spread(sp, phis[i], gs[i], sp["t_final"], want)
-        check_fp32_solve(got, want, spread)
+        resp = noise_spread(sp, phis[i], gs[i], sp["t_final"], want)
+        check_fp32_solve(got, want, resp, sp)
         assert sign_ok(got, want, sp)
 
 

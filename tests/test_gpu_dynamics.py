@@ -74,7 +74,7 @@ def test_rockets_tube_solve(dtype):
     if dtype == "f64":
         assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max()
     else:
-        check_fp32_solve(got, want, noise_spread(spec, phi0, g, 0.4, want))
+        check_fp32_solve(got, want, noise_spread(spec, phi0, g, 0.4, want), spec)
     assert np.all(got <= g + 1e-6 * np.abs(g).max())
 
 

@@ -137,7 +137,7 @@ def test_solve_parity(dtype, diss, varform):
     if dtype == "f64":
         assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max()
     else:
-        check_fp32_solve(got, want, noise_spread(spec, phi0, tgt, 0.3, want))
+        check_fp32_solve(got, want, noise_spread(spec, phi0, tgt, 0.3, want), spec)
     if varform:
         assert (got <= phi0 + 1e-6 * np.abs(phi0).max()).all()
 

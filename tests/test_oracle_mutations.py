@@ -100,6 +100,20 @@ VARIANT_MUTANTS = {
     "normal_speed_bound_signed": ("case ORC_DYN_NORMAL_SPEED: return fabs(c[0]);",
                                   "case ORC_DYN_NORMAL_SPEED: return c[0];"),
 }
+# mistakes in the loss of the differentiation workload (the oracle's Python
+# layer), caught by test_oracle_loss.py
+PY_SRC = os.path.join(os.path.dirname(HERE), "oracle", "__init__.py")
+PY_MUTANTS = {
+    "loss_heaviside_sign": ("vol = np.sum(1.0 / (1.0 + np.exp(f / eps))) * dV",
+                            "vol = np.sum(1.0 / (1.0 + np.exp(-f / eps))) * dV"),
+    "loss_eps_min_dx": ("eps = float(h.max())", "eps = float(h.min())"),
+    "loss_grad_sign": ("g = -Hs * (1.0 - Hs) / eps * dV", "g = Hs * (1.0 - Hs) / eps * dV"),
+    "interp_periodic_clamped": ("i1 = np.mod(i0 + 1, n)", "i1 = np.minimum(i0 + 1, n - 1)"),
+    "interp_weights_swapped": ("w = w * (frac[k] if b else 1.0 - frac[k])",
+                               "w = w * (1.0 - frac[k] if b else frac[k])"),
+    "interp_no_clamp": ("t = np.clip(t, 0.0, n - 1.0)", "t = t"),
+}
+
 PIN_FILE = {**{k: "test_oracle_pins.py" for k in MUTANTS},
             **{k: "test_oracle_adjoint.py" for k in ADJOINT_MUTANTS},
             **{k: "test_oracle_variants.py" for k in VARIANT_MUTANTS}}
@@ -124,4 +138,23 @@ def test_planted_mistake_is_caught(tmp_path, name):
          "-q", "-p", "no:cacheprovider"],
         env=dict(os.environ, LSP_ORACLE_LIB=str(so)), capture_output=True, text=True,
         timeout=600)
+    assert r.returncode != 0, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_planted_loss_mistake_is_caught(tmp_path, orc, name):
+    """The same for the loss, which the oracle computes in Python: the
+    mutated copy of the module is loaded in place of the oracle by the `orc`
+    fixture of a separate pytest run (LSP_ORACLE_PY), on the oracle's
+    library as built."""
+    src = open(PY_SRC).read()
+    old, new = PY_MUTANTS[name]
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
+    m = tmp_path / "oracle_mutant.py"
+    m.write_text(src.replace(old, new, 1))
+    r = subprocess.run(
+        [sys.executable, "-m", "pytest", os.path.join(HERE, "test_oracle_loss.py"), "-x", "-q",
+         "-p", "no:cacheprovider"],
+        env=dict(os.environ, LSP_ORACLE_PY=str(m), LSP_ORACLE_LIB=orc.build()),
+        capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
