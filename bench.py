@@ -116,7 +116,7 @@ def algorithmic(spec) -> tuple[float, float]:
 
 
 KERNEL_SOURCES = ["stencil.cuh", "stage_tiled.cuh", "stage_tiled.inl", "stage_generic.cuh",
-                  "pair2.cuh", "stage_pair.cuh"]
+                  "pair2.cuh", "stage_pair.cuh", "stage_run.cuh", "stage_run.inl"]
 
 
 def kernel_hash() -> str:
@@ -368,11 +368,12 @@ def measure_solve(args, name: str, rank: int, world: int, local_rank: int, clk_t
     bi = h_phi0.numel() * h_phi0.element_size() + (h_g.numel() * h_g.element_size() if h_g is not None else 0)
     bo = h_out[0].numel() * h_out[0].element_size()
     copy = torch.cuda.Stream()
-    P_e2e = P
-    if args.graph:  # the captured graph belongs to phi/g_d; the e2e leg has its own buffers
-        P_e2e = B.Problem(spec, use_graph=False)
-        if tile[0] > 0:
-            P_e2e.set_tile(*tile)
+    P_e2e = [P, P]
+    if args.graph:  # a captured graph belongs to its buffers: one per buffer set
+        P_e2e = [B.Problem(spec, use_graph=True) for _ in range(2)]
+        for Q in P_e2e:
+            if tile[0] > 0:
+                Q.set_tile(*tile)
 
     def e2e_run(K):
         up = [torch.cuda.Event() for _ in range(2)]
@@ -390,7 +391,7 @@ def measure_solve(args, name: str, rank: int, world: int, local_rank: int, clk_t
         upload(0)
         for i in range(K):
             stream.wait_event(up[i % 2])
-            P_e2e.solve(d_phi[i % 2], d_g[i % 2], 0.0, spec["t_final"], stream=stream)
+            P_e2e[i % 2].solve(d_phi[i % 2], d_g[i % 2], 0.0, spec["t_final"], stream=stream)
             done[i % 2].record(stream)
             if i + 1 < K:
                 upload(i + 1)  # after step i-1's download on the copy stream
@@ -564,6 +565,11 @@ def run_batched(args, rank: int, world: int, local_rank: int):
         for a, b in zip(phis, d_phi0):
             a.copy_(b)
 
+    # tile shape per problem dimension, timed on this batch (both launch forms
+    # use the choice made for the timed one)
+    tiles = Bt.autotune(d_phi0, d_g) if args.autotune else 0
+    Bt.opts.batch_tiles = tiles
+    Balt.opts.batch_tiles = tiles
     for _ in range(args.warmup):
         reset()
         stats = Bt.solve(phis, d_g)
@@ -676,6 +682,8 @@ def run_batched(args, rank: int, world: int, local_rank: int):
                    "parallelism": "problems split across ranks" if world > 1 else "single",
                    "l2": "flushed (512 MB write) between timed solves",
                    "launch": "persistent" if persistent else "stage-synchronous (graph)",
+                   "batch_tiles": {f"{d}-D": ["16x16", "32x8", "64x4"][(tiles >> (2 * (d - 2))) & 3]
+                                   for d in (2, 3, 4)},
                    ("stage_synchronous_value" if persistent else "persistent_value"): alt_value,
                    "single_problem_path_value": single_value},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
@@ -882,14 +890,14 @@ def run_shapes(args, rank: int, world: int, local_rank: int):
 
 def adjoint_launches(nsteps: int, rk: int) -> int:
     """Kernels of one gradient evaluation: forward stages, the segment
-    recomputation from sqrt(N) checkpoints, the per-step recomputation of the
-    stage inputs, two adjoint kernels per stage, the GLF argmax, two loss
-    kernels."""
+    recomputation from sqrt(N) checkpoints (which keeps every step's stage
+    inputs; the last step of a segment computes its stage inputs alone), two
+    adjoint kernels per stage, the GLF argmax, two loss kernels."""
     import math
     C = math.ceil(math.sqrt(nsteps))
     K = math.ceil(nsteps / C)
     nseg = math.ceil(nsteps / K)
-    return (nsteps * rk + (nsteps - nseg) * rk + nsteps * (rk - 1) + 2 * rk * nsteps + 1 + 2)
+    return (nsteps * rk + (nsteps - nseg) * rk + nseg * (rk - 1) + 2 * rk * nsteps + 1 + 2)
 
 
 def run_steps(args):

@@ -131,7 +131,13 @@ typedef struct {
                           backward time; here every stage rate L = -Hhat is
                           replaced by min(L, 0), so phi never increases).
                           Independent of tube.                             */
-    int reserved[1];   /* must be zero                                     */
+    int batch_tiles;   /* batched solves: tile of the two fastest axes of
+                          the d-dimensional problems in bits 2(d-2)..2(d-2)+1:
+                          0 = 16 x 16 nodes, 1 = 32 x 8, 2 = 64 x 4 (every
+                          CTA has 256 threads); 0 = 16 x 16 for every
+                          dimension; lsp_batched_autotune picks them; with
+                          local coefficients or the clip the tiles are
+                          16 x 16 whatever this says                       */
 } lsp_solve_opts;
 
 typedef struct {
@@ -305,6 +311,20 @@ lsp_status lsp_hj_solve_noalloc(lsp_grid* grid, const lsp_solve_opts* opts, void
                                 const void* target, double t0, double t_final,
                                 lsp_solve_stats* stats, void* stream);
 
+/* Autotuner of the batched solve's tiles: times the batched solve of these
+ * problems over a short horizon (at most 8 CFL steps each, on scratch
+ * copies of phis: the caller's fields are not modified; the copies are
+ * allocated for the call) for the tile shapes of opts->batch_tiles, one
+ * problem dimension at a time (coordinate descent from opts->batch_tiles),
+ * and returns the fastest in *batch_tiles for the caller to store in
+ * opts->batch_tiles.  Arguments as for lsp_hj_solve_batched; the workspace
+ * from lsp_batched_workspace_size serves every tile choice.  Waits for the
+ * GPU. */
+lsp_status lsp_batched_autotune(int nprob, lsp_grid* const* grids, const lsp_solve_opts* opts,
+                                const void* const* phis, const void* const* targets,
+                                const double* t_final, void* workspace, size_t workspace_bytes,
+                                void* stream, int* batch_tiles);
+
 /* Batched solves: nprob independent problems (own grid, dynamics, CFL step
  * and t_final each) advanced together, problem i from t = 0 to t_final[i].
  * One kernel launch advances one RK stage of every problem that still has
@@ -351,8 +371,10 @@ lsp_status lsp_hj_solve_batched(int nprob, lsp_grid* const* grids, const lsp_sol
  * through H, through the GLF coefficients and through dt.
  *
  * lsp_adjoint_workspace_size: bytes for ncheck checkpoints (0: ceil(sqrt
- *   nsteps)), a segment of ceil(nsteps/ncheck) recomputed states, the stage
- *   fields, five adjoint fields and 7*ndim coefficient fields.
+ *   nsteps)), a segment of ceil(nsteps/ncheck) recomputed states with the
+ *   RK stage inputs of each (rk_order - 1 fields per state, kept by the
+ *   recomputation for the reverse sweep), the stage fields, five adjoint
+ *   fields and 7*ndim coefficient fields.
  * lsp_hj_solve_ckpt: the forward solve (phi in place), storing checkpoints
  *   in the workspace.  Asynchronous.
  * lsp_hj_adjoint: the reverse sweep from the checkpoints left in the same

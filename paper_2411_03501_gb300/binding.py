@@ -28,7 +28,7 @@ EXPORTS = [
     "lsp_set_dynamics", "lsp_get_alpha", "lsp_workspace_size", "lsp_cfl_dt", "lsp_hj_rate",
     "lsp_hj_step", "lsp_hj_solve", "lsp_check_status", "lsp_hj_solve_noalloc",
     "lsp_set_tile", "lsp_get_tile", "lsp_autotune", "lsp_batched_workspace_size",
-    "lsp_hj_solve_batched", "lsp_adjoint_workspace_size", "lsp_hj_solve_ckpt", "lsp_hj_adjoint",
+    "lsp_hj_solve_batched", "lsp_batched_autotune", "lsp_adjoint_workspace_size", "lsp_hj_solve_ckpt", "lsp_hj_adjoint",
     "lsp_loss_tube", "lsp_debug_stall_problem", "lsp_shape_sphere", "lsp_shape_box",
     "lsp_shape_quadric", "lsp_shape_halfspace", "lsp_shape_op",
 ]
@@ -55,7 +55,7 @@ class lsp_solve_opts(ctypes.Structure):
         ("batch_wait_ms", ctypes.c_int),
         ("diss", ctypes.c_int),
         ("varform", ctypes.c_int),
-        ("reserved", ctypes.c_int * 1),
+        ("batch_tiles", ctypes.c_int),
     ]
 
 
@@ -121,13 +121,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.lsp_batched_workspace_size.argtypes = [ctypes.c_int, pp, op, ctypes.POINTER(sz)]
     L.lsp_hj_solve_batched.argtypes = [ctypes.c_int, pp, op, pp, pp, dp, vp, sz,
                                        ctypes.POINTER(lsp_solve_stats), vp]
+    L.lsp_batched_autotune.argtypes = [ctypes.c_int, pp, op, pp, pp, dp, vp, sz, vp, ip]
     ci = ctypes.c_int
     L.lsp_adjoint_workspace_size.argtypes = [vp, op, ci, ci, ctypes.POINTER(sz)]
     L.lsp_hj_solve_ckpt.argtypes = [vp, op, vp, vp, ci, ci, vp, sz, vp]
     L.lsp_hj_adjoint.argtypes = [vp, op, vp, ci, ci, vp, vp, vp, dp, vp, sz, vp]
     L.lsp_loss_tube.argtypes = [vp, ci, vp, vp, ci, vp, vp, vp]
     for name in ("lsp_set_tile", "lsp_get_tile", "lsp_autotune", "lsp_batched_workspace_size",
-                 "lsp_hj_solve_batched", "lsp_adjoint_workspace_size", "lsp_hj_solve_ckpt",
+                 "lsp_hj_solve_batched", "lsp_batched_autotune", "lsp_adjoint_workspace_size", "lsp_hj_solve_ckpt",
                  "lsp_hj_adjoint", "lsp_loss_tube"):
         getattr(L, name).restype = ctypes.c_int
     for name in ("lsp_grid_create", "lsp_set_dynamics", "lsp_get_alpha", "lsp_workspace_size",
@@ -297,6 +298,21 @@ def lsp_hj_solve_batched(grids, opts, phis, targets, t_final, workspace, stream=
              "t_end": s.t_end} for s in st]
 
 
+def lsp_batched_autotune(grids, opts, phis, targets, t_final, workspace, stream=None) -> int:
+    """The batch_tiles value (tile shape per problem dimension) that ran the
+    batched solve of these problems fastest over a short horizon; phis are
+    not modified."""
+    n = len(grids)
+    P = (ctypes.c_void_p * n)(*[t.data_ptr() for t in phis])
+    T = (ctypes.c_void_p * n)(*[t.data_ptr() for t in targets]) if targets is not None else None
+    tf = (ctypes.c_double * n)(*[float(v) for v in t_final])
+    out = ctypes.c_int(0)
+    _check(load().lsp_batched_autotune(n, _handles(grids), ctypes.byref(opts), P, T, tf,
+                                       _ptr(workspace), _nbytes(workspace), _stream(stream),
+                                       ctypes.byref(out)))
+    return int(out.value)
+
+
 def lsp_adjoint_workspace_size(grid: Grid, opts, nsteps: int, ncheck: int = 0) -> int:
     b = ctypes.c_size_t()
     _check(load().lsp_adjoint_workspace_size(grid.handle, ctypes.byref(opts), int(nsteps),
@@ -331,7 +347,7 @@ class Batch:
     :mod:`workloads`) sharing scheme, RK order, CFL and tube."""
 
     def __init__(self, specs, device="cuda", check_finite=False, use_graph=True, chunk=0,
-                 persistent=False, wait_ms=0):
+                 persistent=False, wait_ms=0, tiles=0):
         import torch
         self.specs = specs
         self.grids = []
@@ -347,6 +363,7 @@ class Batch:
         self.opts.batch_chunk = int(chunk)
         self.opts.batch_persistent = 1 if persistent else 0
         self.opts.batch_wait_ms = int(wait_ms)
+        self.opts.batch_tiles = int(tiles)
         nbytes = lsp_batched_workspace_size(self.grids, self.opts)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
 
@@ -354,6 +371,14 @@ class Batch:
         tf = [sp["t_final"] for sp in self.specs] if t_final is None else t_final
         return lsp_hj_solve_batched(self.grids, self.opts, phis, targets, tf, self.workspace,
                                     stream)
+
+    def autotune(self, phis, targets=None, t_final=None, stream=None) -> int:
+        """Pick the tile shape per problem dimension (lsp_batched_autotune)
+        and keep it for later solves; returns the batch_tiles value."""
+        tf = [sp["t_final"] for sp in self.specs] if t_final is None else t_final
+        self.opts.batch_tiles = lsp_batched_autotune(self.grids, self.opts, phis, targets, tf,
+                                                     self.workspace, stream)
+        return self.opts.batch_tiles
 
 
 def lsp_check_status(workspace, stream=None):

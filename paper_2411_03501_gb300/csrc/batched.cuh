@@ -45,75 +45,116 @@ __device__ __forceinline__ void batch_stage_args(const BatchProblem& P, int step
 // variant for local coefficients or the clip, state-only bounds), the scalar
 // body otherwise.
 template <int NDIM, int SCHEME, int DYN, bool COH, bool LOCAL>
-__device__ __forceinline__ void batch_body(const StageArgs<float>& sa, int bx, int by, int chunk,
-                                           int outer, int ch, float* tile, int tx, int ty)
+__device__ __forceinline__ void batch_body(const StageArgs<float>& sa, int TB, int TA, int bx,
+                                           int by, int chunk, int outer, int ch, float* tile,
+                                           int tx, int ty)
 {
     if constexpr (SCHEME == WENO5 && (!LOCAL || DYN != QUADRATIC))
-        tiled_pair_body<NDIM, DYN, true, COH, WENO5, LOCAL>(sa, kBatchTB, kBatchTA, bx, by, chunk,
-                                                            outer, ch, tile, tx, ty);
+        tiled_pair_body<NDIM, DYN, true, COH, WENO5, LOCAL>(sa, TB, TA, bx, by, chunk, outer, ch,
+                                                            tile, tx, ty);
     else
-        tiled_stage_body<NDIM, SCHEME, DYN, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by,
-                                                               chunk, outer, ch, tile, tx, ty);
+        tiled_stage_body<NDIM, SCHEME, DYN, float, COH, LOCAL>(sa, TB, TA, bx, by, chunk, outer,
+                                                               ch, tile, tx, ty);
 }
 
 // Shared tile of a batched CTA: two double-buffered planes, four for the
-// paired body (WENO5).
+// paired body (WENO5), of the largest tile shape.
 template <int SCHEME, bool LOCAL>
 __host__ __device__ constexpr int batch_tile_floats()
 {
-    return (SCHEME == WENO5 ? 4 : 2) * (kBatchTA + 2 * ghost_width(SCHEME)) *
-           (kBatchTB + 2 * ghost_width(SCHEME));
+    return (SCHEME == WENO5 ? 4 : 2) * batch_max_tile(ghost_width(SCHEME));
 }
 
-template <int SCHEME, bool COH, bool LOCAL>
-__device__ __forceinline__ void batch_tile(const BatchProblem& P, const StageArgs<float>& sa,
-                                           int local, float* tile)
+// Problem classes a batched kernel is compiled for: every supported
+// (dimension, dynamics) pair, or only 2-D normal speed and 3-D air3d (the
+// mixed workload of reachability problems), so that the kernel's register
+// allocation is that of those two bodies alone.
+enum {
+    kClsAll = kBatchClsAll,
+    kClsNormal2Air3 = kBatchClsNormal2Air3,
+    kClsNormal2Air3x16 = kBatchClsNormal2Air3x16  // the same, 16 x 16 tiles only
+};
+__host__ __device__ constexpr bool cls_has(int cls, int ndim, int dyn)
+{
+    return cls == kClsAll || (ndim == 2 && dyn == NORMAL_SPEED) || (ndim == 3 && dyn == AIR3D);
+}
+
+// One tile of shape TB x TA (compile-time: the bodies' index arithmetic
+// folds the tile extents).
+template <int SCHEME, bool COH, bool LOCAL, int CLS, int TB, int TA>
+__device__ __forceinline__ void batch_tile_shape(const BatchProblem& P, const StageArgs<float>& sa,
+                                                 int local, float* tile)
 {
     const int bx = local % P.nbx;
     const int by = (local / P.nbx) % P.nby;
     const int z = local / (P.nbx * P.nby);
     const int chunk = z % P.nchunks, outer = z / P.nchunks;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int ty = threadIdx.x / TB, tx = threadIdx.x - ty * TB;
     switch (P.ndim * 8 + P.dyn) {
     case 2 * 8 + NORMAL_SPEED:
-        tiled_stage_body<2, SCHEME, NORMAL_SPEED, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by, 0, 0, 1, tile, tx, ty);
+        if constexpr (cls_has(CLS, 2, NORMAL_SPEED))
+            tiled_stage_body<2, SCHEME, NORMAL_SPEED, float, COH, LOCAL>(sa, TB, TA, bx, by, 0, 0, 1, tile, tx, ty);
         break;
     case 2 * 8 + TRANSLATE:
-        tiled_stage_body<2, SCHEME, TRANSLATE, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by, 0, 0, 1, tile, tx, ty);
+        if constexpr (cls_has(CLS, 2, TRANSLATE))
+            tiled_stage_body<2, SCHEME, TRANSLATE, float, COH, LOCAL>(sa, TB, TA, bx, by, 0, 0, 1, tile, tx, ty);
         break;
     case 3 * 8 + NORMAL_SPEED:
-        batch_body<3, SCHEME, NORMAL_SPEED, COH, LOCAL>(sa, bx, by, chunk, 0, P.ch, tile, tx, ty);
+        if constexpr (cls_has(CLS, 3, NORMAL_SPEED))
+            batch_body<3, SCHEME, NORMAL_SPEED, COH, LOCAL>(sa, TB, TA, bx, by, chunk, 0, P.ch, tile, tx, ty);
         break;
     case 3 * 8 + TRANSLATE:
-        batch_body<3, SCHEME, TRANSLATE, COH, LOCAL>(sa, bx, by, chunk, 0, P.ch, tile, tx, ty);
+        if constexpr (cls_has(CLS, 3, TRANSLATE))
+            batch_body<3, SCHEME, TRANSLATE, COH, LOCAL>(sa, TB, TA, bx, by, chunk, 0, P.ch, tile, tx, ty);
         break;
     case 3 * 8 + AIR3D:
-        batch_body<3, SCHEME, AIR3D, COH, LOCAL>(sa, bx, by, chunk, 0, P.ch, tile, tx, ty);
+        if constexpr (cls_has(CLS, 3, AIR3D))
+            batch_body<3, SCHEME, AIR3D, COH, LOCAL>(sa, TB, TA, bx, by, chunk, 0, P.ch, tile, tx, ty);
         break;
     case 3 * 8 + ROCKETS:
-        batch_body<3, SCHEME, ROCKETS, COH, LOCAL>(sa, bx, by, chunk, 0, P.ch, tile, tx, ty);
+        if constexpr (cls_has(CLS, 3, ROCKETS))
+            batch_body<3, SCHEME, ROCKETS, COH, LOCAL>(sa, TB, TA, bx, by, chunk, 0, P.ch, tile, tx, ty);
         break;
     case 2 * 8 + DOUBLE_INT:
-        tiled_stage_body<2, SCHEME, DOUBLE_INT, float, COH, LOCAL>(sa, kBatchTB, kBatchTA, bx, by, 0, 0, 1, tile, tx, ty);
+        if constexpr (cls_has(CLS, 2, DOUBLE_INT))
+            tiled_stage_body<2, SCHEME, DOUBLE_INT, float, COH, LOCAL>(sa, TB, TA, bx, by, 0, 0, 1, tile, tx, ty);
         break;
     case 4 * 8 + NORMAL_SPEED:
-        batch_body<4, SCHEME, NORMAL_SPEED, COH, LOCAL>(sa, bx, by, chunk, outer, P.ch, tile, tx, ty);
+        if constexpr (cls_has(CLS, 4, NORMAL_SPEED))
+            batch_body<4, SCHEME, NORMAL_SPEED, COH, LOCAL>(sa, TB, TA, bx, by, chunk, outer, P.ch, tile, tx, ty);
         break;
     case 4 * 8 + TRANSLATE:
-        batch_body<4, SCHEME, TRANSLATE, COH, LOCAL>(sa, bx, by, chunk, outer, P.ch, tile, tx, ty);
+        if constexpr (cls_has(CLS, 4, TRANSLATE))
+            batch_body<4, SCHEME, TRANSLATE, COH, LOCAL>(sa, TB, TA, bx, by, chunk, outer, P.ch, tile, tx, ty);
         break;
     case 4 * 8 + CAR4D:
-        batch_body<4, SCHEME, CAR4D, COH, LOCAL>(sa, bx, by, chunk, outer, P.ch, tile, tx, ty);
+        if constexpr (cls_has(CLS, 4, CAR4D))
+            batch_body<4, SCHEME, CAR4D, COH, LOCAL>(sa, TB, TA, bx, by, chunk, outer, P.ch, tile, tx, ty);
         break;
     default:
         break;  // rejected on the host
     }
 }
 
+template <int SCHEME, bool COH, bool LOCAL, int CLS = kClsAll>
+__device__ __forceinline__ void batch_tile(const BatchProblem& P, const StageArgs<float>& sa,
+                                           int local, float* tile)
+{
+    static_assert(kBatchShapes[1][0] == 32 && kBatchShapes[2][0] == 64, "tile shapes");
+    if constexpr (LOCAL || CLS == kClsNormal2Air3x16) {  // 16 x 16 tiles only (local
+                                                          // coefficients / the clip: see the plan)
+        batch_tile_shape<SCHEME, COH, LOCAL, CLS, 16, 16>(P, sa, local, tile);
+        return;
+    }
+    if (P.tb == 32) batch_tile_shape<SCHEME, COH, LOCAL, CLS, 32, 8>(P, sa, local, tile);
+    else if (P.tb == 64) batch_tile_shape<SCHEME, COH, LOCAL, CLS, 64, 4>(P, sa, local, tile);
+    else batch_tile_shape<SCHEME, COH, LOCAL, CLS, 16, 16>(P, sa, local, tile);
+}
+
 // One RK stage of every active problem: CTA i runs tile i - block_start of
 // problem block_prob[i].
-template <int SCHEME, bool LOCAL>
-__global__ void __launch_bounds__(kBatchTB * kBatchTA, 3)
+template <int SCHEME, bool LOCAL, int CLS>
+__global__ void __launch_bounds__(kBatchThreads, 3)
     stage_batched_kernel(const BatchProblem* __restrict__ probs, const int* __restrict__ block_prob,
                          int step, int stage, int rk)
 {
@@ -122,10 +163,10 @@ __global__ void __launch_bounds__(kBatchTB * kBatchTA, 3)
     __shared__ __align__(16) float tile[batch_tile_floats<SCHEME, LOCAL>()];
     const int p = block_prob[blockIdx.x];
     const BatchProblem& P = probs[p];
-    const int tid = threadIdx.y * kBatchTB + threadIdx.x;
+    const int tid = threadIdx.x;
     if (tid == 0) batch_stage_args(P, step, stage, rk, sa);
     __syncthreads();
-    batch_tile<SCHEME, false, LOCAL>(P, sa, blockIdx.x - P.block_start, tile);
+    batch_tile<SCHEME, false, LOCAL, CLS>(P, sa, blockIdx.x - P.block_start, tile);
 }
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -143,8 +184,8 @@ __device__ __forceinline__ unsigned long long global_ns()
 // the problem's completion counter; the wait is bounded by wait_ns, after
 // which it raises kFlagTimeout, sets the abort flag (other waiters leave at
 // once) and stops: the launch always ends.
-template <int SCHEME, bool LOCAL>
-__global__ void __launch_bounds__(kBatchTB * kBatchTA, 3)
+template <int SCHEME, bool LOCAL, int CLS>
+__global__ void __launch_bounds__(kBatchThreads, 3)
     stage_batched_persistent(const BatchProblem* __restrict__ probs,
                              const int* __restrict__ block_prob,
                              const BatchSegment* __restrict__ segs, int nseg, int rk,
@@ -155,7 +196,7 @@ __global__ void __launch_bounds__(kBatchTB * kBatchTA, 3)
     __shared__ StageArgs<float> sa;
     __shared__ __align__(16) float tile[batch_tile_floats<SCHEME, LOCAL>()];
     __shared__ int s_p, s_local, s_stop;
-    const int tid = threadIdx.y * kBatchTB + threadIdx.x;
+    const int tid = threadIdx.x;
     const long long total = segs[nseg].item_start;
     for (;;) {
         if (tid == 0) {
@@ -204,7 +245,7 @@ __global__ void __launch_bounds__(kBatchTB * kBatchTA, 3)
         }
         __syncthreads();
         if (s_stop) break;
-        batch_tile<SCHEME, true, LOCAL>(probs[s_p], sa, s_local, tile);
+        batch_tile<SCHEME, true, LOCAL, CLS>(probs[s_p], sa, s_local, tile);
         __syncthreads();
         if (tid == 0) {
             __threadfence();  // release this tile's stores before counting it done
@@ -213,46 +254,45 @@ __global__ void __launch_bounds__(kBatchTB * kBatchTA, 3)
     }
 }
 
-template <bool LOCAL>
-cudaError_t launch_batched_persistent_t(int scheme, const BatchProblem* probs, const int* block_prob,
-                                      const BatchSegment* segs, int nseg, int rk,
-                                      unsigned int* done, PersistCtl* pc, Ctl* ctl,
-                                      unsigned long long wait_ns, cudaStream_t s)
+// The launches of one (scheme, local, class set) instantiation.  They are
+// instantiated explicitly in separate translation units (batched_*.cu) so
+// that the kernels compile in parallel; batched.cu dispatches to them.
+template <int SCHEME, bool LOCAL, int CLS>
+cudaError_t launch_batched_k(const BatchProblem* probs, const int* block_prob, int nblocks,
+                             int step, int stage, int rk, cudaStream_t s)
 {
-    const void* fn = nullptr;
-    switch (scheme) {
-    case UPWIND1: fn = (const void*)stage_batched_persistent<UPWIND1, LOCAL>; break;
-    case ENO2: fn = (const void*)stage_batched_persistent<ENO2, LOCAL>; break;
-    case ENO3: fn = (const void*)stage_batched_persistent<ENO3, LOCAL>; break;
-    case WENO5: fn = (const void*)stage_batched_persistent<WENO5, LOCAL>; break;
-    default: return cudaErrorInvalidValue;
-    }
-    int dev = 0, nsm = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (!e) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchTB * kBatchTA, 0);
+    if (nblocks <= 0) return cudaSuccess;
+    stage_batched_kernel<SCHEME, LOCAL, CLS><<<nblocks, dim3(kBatchThreads, 1, 1), 0, s>>>(
+        probs, block_prob, step, stage, rk);
+    return cudaGetLastError();
+}
+
+template <int SCHEME, bool LOCAL, int CLS>
+cudaError_t launch_persistent_k(const BatchProblem* probs, const int* block_prob,
+                                const BatchSegment* segs, int nseg, int rk, unsigned int* done,
+                                PersistCtl* pc, Ctl* ctl, unsigned long long wait_ns,
+                                cudaStream_t s)
+{
+    const void* fn = (const void*)stage_batched_persistent<SCHEME, LOCAL, CLS>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, 0);
     if (e) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    dim3 grid(nsm * per_sm), block(kBatchTB, kBatchTA, 1);
+    dim3 grid(sm_count() * per_sm), block(kBatchThreads, 1, 1);
     void* args[] = {(void*)&probs, (void*)&block_prob, (void*)&segs, (void*)&nseg, (void*)&rk,
                     (void*)&done, (void*)&pc, (void*)&ctl, (void*)&wait_ns};
     return cudaLaunchCooperativeKernel(fn, grid, block, args, 0, s);
 }
 
-template <bool LOCAL>
-cudaError_t launch_batched_t(int scheme, const BatchProblem* probs, const int* block_prob, int nblocks,
-                           int step, int stage, int rk, cudaStream_t s)
-{
-    if (nblocks <= 0) return cudaSuccess;
-    dim3 block(kBatchTB, kBatchTA, 1);
-    switch (scheme) {
-    case UPWIND1: stage_batched_kernel<UPWIND1, LOCAL><<<nblocks, block, 0, s>>>(probs, block_prob, step, stage, rk); break;
-    case ENO2: stage_batched_kernel<ENO2, LOCAL><<<nblocks, block, 0, s>>>(probs, block_prob, step, stage, rk); break;
-    case ENO3: stage_batched_kernel<ENO3, LOCAL><<<nblocks, block, 0, s>>>(probs, block_prob, step, stage, rk); break;
-    case WENO5: stage_batched_kernel<WENO5, LOCAL><<<nblocks, block, 0, s>>>(probs, block_prob, step, stage, rk); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
+#define LSP_BATCHED_INSTANTIATE_STAGE(SCHEME, LOCAL, CLS)                                         \
+    template cudaError_t launch_batched_k<SCHEME, LOCAL, CLS>(                                    \
+        const BatchProblem*, const int*, int, int, int, int, cudaStream_t);
+#define LSP_BATCHED_INSTANTIATE_PERSISTENT(SCHEME, LOCAL, CLS)                                    \
+    template cudaError_t launch_persistent_k<SCHEME, LOCAL, CLS>(                                 \
+        const BatchProblem*, const int*, const BatchSegment*, int, int, unsigned int*,           \
+        PersistCtl*, Ctl*, unsigned long long, cudaStream_t);
+#define LSP_BATCHED_INSTANTIATE(SCHEME, LOCAL, CLS)                                               \
+    LSP_BATCHED_INSTANTIATE_STAGE(SCHEME, LOCAL, CLS)                                             \
+    LSP_BATCHED_INSTANTIATE_PERSISTENT(SCHEME, LOCAL, CLS)
 
 }  // namespace lsp

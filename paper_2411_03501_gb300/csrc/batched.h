@@ -16,9 +16,24 @@ struct BatchProblem {
     int ndim, dyn;
     int ch, nbx, nby, nchunks;  // tile grid: x-tiles, y-tiles, chunks along the march
     int block_start, nblocks;   // this problem's CTAs in the launch
+    int tb, ta;                 // tile of the two fastest axes (tb x ta = kBatchThreads)
 };
 
-constexpr int kBatchTB = 16, kBatchTA = 16;
+// Every batched CTA has kBatchThreads threads; each problem's tile of its two
+// fastest axes is one of kBatchShapes (chosen per problem dimension by
+// lsp_solve_opts.batch_tiles), thread t covering (t % tb, t / tb).
+constexpr int kBatchThreads = 256;
+constexpr int kBatchNumShapes = 3;
+constexpr int kBatchShapes[kBatchNumShapes][2] = {{16, 16}, {32, 8}, {64, 4}};
+// the largest haloed tile of the shapes, in floats, for ghost width G
+__host__ __device__ constexpr int batch_max_tile(int G)
+{
+    return (16 + 2 * G) * (16 + 2 * G) > (8 + 2 * G) * (32 + 2 * G)
+               ? ((16 + 2 * G) * (16 + 2 * G) > (4 + 2 * G) * (64 + 2 * G)
+                      ? (16 + 2 * G) * (16 + 2 * G) : (4 + 2 * G) * (64 + 2 * G))
+               : ((8 + 2 * G) * (32 + 2 * G) > (4 + 2 * G) * (64 + 2 * G)
+                      ? (8 + 2 * G) * (32 + 2 * G) : (4 + 2 * G) * (64 + 2 * G));
+}
 
 // Persistent batched launch: work items (step k, stage s, tile b) are handed
 // out in this order by one counter; the steps split into segments with a

@@ -46,21 +46,22 @@ struct BatchProblem;
 struct BatchSegment;
 struct PersistCtl;
 // local: the problems use local dissipation coefficients or the variational
-// clip (batched_local.cu's instantiation).
+// clip (batched_local.cu's instantiation).  cls: the class set the kernel is
+// compiled for (kBatchClsNormal2Air3: every problem is 2-D normal speed or
+// 3-D air3d; kBatchClsAll otherwise; local kernels cover every class).
+// kBatchClsNormal2Air3x16: the same two classes, every tile 16 x 16.
+enum { kBatchClsAll = 0, kBatchClsNormal2Air3 = 1, kBatchClsNormal2Air3x16 = 2 };
 cudaError_t launch_batched(int scheme, const BatchProblem* probs, const int* block_prob, int nblocks,
-                           int step, int stage, int rk, bool local, cudaStream_t s);
-cudaError_t launch_batched_local(int scheme, const BatchProblem* probs, const int* block_prob,
-                                 int nblocks, int step, int stage, int rk, cudaStream_t s);
+                           int step, int stage, int rk, bool local, int cls, cudaStream_t s);
 // The whole batched solve as one cooperative launch of resident CTAs.
 cudaError_t launch_batched_persistent(int scheme, const BatchProblem* probs, const int* block_prob,
                                       const BatchSegment* segs, int nseg, int rk,
                                       unsigned int* done, PersistCtl* pc, Ctl* ctl,
-                                      unsigned long long wait_ns, bool local, cudaStream_t s);
-cudaError_t launch_batched_persistent_local(int scheme, const BatchProblem* probs,
-                                            const int* block_prob, const BatchSegment* segs,
-                                            int nseg, int rk, unsigned int* done, PersistCtl* pc,
-                                            Ctl* ctl, unsigned long long wait_ns, cudaStream_t s);
-void batch_tile_dims(int* tb, int* ta);
+                                      unsigned long long wait_ns, bool local, int cls,
+                                      cudaStream_t s);
+// Tile shape `shape` (0: 16 x 16, 1: 32 x 8, 2: 64 x 4) of batched problems;
+// false for other values.
+bool batch_tile_dims(int shape, int* tb, int* ta);
 bool batch_supported(int ndim, int dyn);
 
 // Implicit-surface primitives and set operations (shapes.cu).

@@ -82,8 +82,10 @@ lsp_status check_opts(const lsp_grid* g, const lsp_solve_opts* o)
     if (o->scheme < LSP_UPWIND1 || o->scheme > LSP_WENO5) return fail(LSP_EINVAL, "bad scheme");
     if (o->dtype != LSP_F32 && o->dtype != LSP_F64) return fail(LSP_EINVAL, "bad dtype");
     if (!(o->cfl > 0.0 && o->cfl <= 1.0)) return fail(LSP_EINVAL, "cfl must be in (0, 1]");
-    for (int i = 0; i < 1; ++i)
-        if (o->reserved[i]) return fail(LSP_EINVAL, "reserved option fields must be zero");
+    for (int d = 2; d <= 4; ++d)
+        if (((o->batch_tiles >> (2 * (d - 2))) & 3) == 3)
+            return fail(LSP_EINVAL, "batch_tiles: shape 3 is not defined (dimension %d)", d);
+    if (o->batch_tiles >> 6) return fail(LSP_EINVAL, "batch_tiles: bits above 5 must be zero");
     if (o->diss < LSP_DISS_GLF || o->diss > LSP_DISS_LLLF) return fail(LSP_EINVAL, "bad diss");
     if (o->varform != 0 && o->varform != 1) return fail(LSP_EINVAL, "varform must be 0 or 1");
     if (o->batch_chunk < 0) return fail(LSP_EINVAL, "batch_chunk must be >= 0");
@@ -227,11 +229,14 @@ lsp_status enqueue_stage(const lsp_grid* g, const lsp_solve_opts* o, lsp::Ctl* c
 // One TVD-RK step of size dt, phi in place (Sec. V-A), tube in the last stage.
 template <typename R>
 lsp_status enqueue_step(const lsp_grid* g, const lsp_solve_opts* o, R* phi, const R* target,
-                        double dt, void* ws, cudaStream_t st)
+                        double dt, void* ws, cudaStream_t st, R* w1_at = nullptr,
+                        R* w2_at = nullptr)
 {
+    // stage fields: the workspace's, or the caller's (w1_at, w2_at: the
+    // adjoint keeps a segment's stage inputs)
     lsp::Ctl* ctl = (lsp::Ctl*)ws;
-    R* w1 = (R*)((char*)ws + lsp::kCtlBytes);
-    R* w2 = (R*)((char*)w1 + round256((size_t)g->npts * sizeof(R)));
+    R* w1 = w1_at ? w1_at : (R*)((char*)ws + lsp::kCtlBytes);
+    R* w2 = w2_at ? w2_at : (R*)((char*)ws + lsp::kCtlBytes + round256((size_t)g->npts * sizeof(R)));
     const bool tube = o->tube != 0;
     lsp_status s;
     switch (o->rk_order) {
@@ -889,6 +894,7 @@ struct BatchPlanEntry {
     int nsteps;
     double dt, dt_last;
     int nbx, nby, nchunks, ch, nblocks;
+    int tb, ta;          // tile of the two fastest axes
     size_t field_bytes;  // one stage field, rounded to 256
 };
 
@@ -933,11 +939,12 @@ size_t batch_persist_bytes(int nprob)
 int g_stall_problem = -1;
 
 // Tile grid and field sizes of every problem; the total workspace bytes.
+// any_shape: size the block table for the largest tile count over every
+// shape (a workspace that serves any opts->batch_tiles).
 void batch_geometry(int nprob, lsp_grid* const* grids, const lsp_solve_opts* o,
-                    std::vector<BatchPlanEntry>& plan, size_t* bytes, long long* total_blocks)
+                    std::vector<BatchPlanEntry>& plan, size_t* bytes, long long* total_blocks,
+                    bool any_shape = false)
 {
-    int tb, ta;
-    lsp::batch_tile_dims(&tb, &ta);
     const int chunk = o->batch_chunk > 0 ? o->batch_chunk : 32;
     plan.resize(nprob);
     size_t fields = 0;
@@ -949,20 +956,36 @@ void batch_geometry(int nprob, lsp_grid* const* grids, const lsp_solve_opts* o,
         e.p = i;
         e.nsteps = 0;
         e.dt = e.dt_last = 0.0;
-        e.nbx = (g->n[d - 1] + tb - 1) / tb;
-        e.nby = (g->n[d - 2] + ta - 1) / ta;
-        if (d >= 3) {
-            const int nS = g->n[d - 3];
-            e.ch = std::min(chunk, nS);
-            e.nchunks = (nS + e.ch - 1) / e.ch;
-        } else {
-            e.ch = 1;
-            e.nchunks = 1;
+        // the local-coefficient / clipped kernels are compiled for 16 x 16 tiles
+        const bool local = o->diss != LSP_DISS_GLF || o->varform;
+        const int shape = local ? 0 : (o->batch_tiles >> (2 * (d - 2))) & 3;
+        long long nb_max = 0;
+        for (int sh = 0; sh < 3; ++sh) {
+            if (!any_shape && sh != shape) continue;
+            int tb = 16, ta = 16;
+            lsp::batch_tile_dims(sh, &tb, &ta);
+            const int nbx = (g->n[d - 1] + tb - 1) / tb, nby = (g->n[d - 2] + ta - 1) / ta;
+            int ch = 1, nchunks = 1;
+            if (d >= 3) {
+                const int nS = g->n[d - 3];
+                ch = std::min(chunk, nS);
+                nchunks = (nS + ch - 1) / ch;
+            }
+            const long long nb = (long long)nbx * nby * nchunks * (d == 4 ? g->n[0] : 1);
+            nb_max = std::max(nb_max, nb);
+            if (sh == shape) {
+                e.tb = tb;
+                e.ta = ta;
+                e.nbx = nbx;
+                e.nby = nby;
+                e.ch = ch;
+                e.nchunks = nchunks;
+                e.nblocks = (int)nb;
+            }
         }
-        e.nblocks = e.nbx * e.nby * e.nchunks * (d == 4 ? g->n[0] : 1);
         e.field_bytes = round256((size_t)g->npts * sizeof(float));
         fields += nfields(o->rk_order) * e.field_bytes;
-        blocks += e.nblocks;
+        blocks += any_shape ? nb_max : e.nblocks;
     }
     *total_blocks = blocks;
     *bytes = lsp::kCtlBytes + round256((size_t)nprob * sizeof(lsp::BatchProblem)) +
@@ -978,7 +1001,7 @@ lsp_status solve_batched_persistent(int nprob, const lsp_solve_opts* o,
                                     const std::vector<int>& prefix, const lsp::BatchProblem* d_table,
                                     const int* d_block_prob, lsp::PersistCtl* d_pc,
                                     unsigned int* d_done, lsp::BatchSegment* d_segs, lsp::Ctl* ctl,
-                                    void* ws, cudaStream_t st)
+                                    void* ws, int cls, cudaStream_t st)
 {
     const int rk = o->rk_order;
     std::vector<lsp::BatchSegment> segs;
@@ -1026,7 +1049,7 @@ lsp_status solve_batched_persistent(int nprob, const lsp_solve_opts* o,
         (unsigned long long)(o->batch_wait_ms > 0 ? o->batch_wait_ms : 1000) * 1000000ULL;
     e = lsp::launch_batched_persistent(o->scheme, d_table, d_block_prob, d_segs, nseg, rk, d_done,
                                        d_pc, ctl, wait_ns, o->diss != LSP_DISS_GLF || o->varform,
-                                       st);
+                                       cls, st);
     if (e) return cuda_fail(e, "persistent batched kernel");
     return LSP_OK;
 }
@@ -1050,7 +1073,7 @@ lsp_status lsp_batched_workspace_size(int nprob, lsp_grid* const* grids, const l
     if (s) return s;
     std::vector<BatchPlanEntry> plan;
     long long blocks = 0;
-    batch_geometry(nprob, grids, o, plan, bytes, &blocks);
+    batch_geometry(nprob, grids, o, plan, bytes, &blocks, true);
     return LSP_OK;
 }
 
@@ -1144,6 +1167,8 @@ lsp_status lsp_hj_solve_batched(int nprob, lsp_grid* const* grids, const lsp_sol
         P.nbx = e.nbx;
         P.nby = e.nby;
         P.nchunks = e.nchunks;
+        P.tb = e.tb;
+        P.ta = e.ta;
         P.block_start = prefix[j];
         P.nblocks = e.nblocks;
         prefix[j + 1] = prefix[j] + e.nblocks;
@@ -1157,9 +1182,19 @@ lsp_status lsp_hj_solve_batched(int nprob, lsp_grid* const* grids, const lsp_sol
                                 cudaMemcpyHostToDevice, st);
     if (e) return cuda_fail(e, "upload batch table");
 
+    // the class set the kernels are compiled for: 2-D normal speed and 3-D
+    // air3d alone when those are the only problems, else every class
+    int cls = lsp::kBatchClsNormal2Air3;
+    for (int i = 0; i < nprob; ++i) {
+        const lsp_grid* g = grids[i];
+        if (!((g->ndim == 2 && g->dyn == LSP_DYN_NORMAL_SPEED) ||
+              (g->ndim == 3 && g->dyn == LSP_DYN_AIR3D)))
+            cls = lsp::kBatchClsAll;
+    }
+    if (cls == lsp::kBatchClsNormal2Air3 && o->batch_tiles == 0) cls = lsp::kBatchClsNormal2Air3x16;
     if (o->batch_persistent) {
         s = solve_batched_persistent(nprob, o, order, prefix, d_table, d_block_prob, d_pc, d_done,
-                                     d_segs, ctl, ws, st);
+                                     d_segs, ctl, ws, cls, st);
         if (s) return s;
         if (o->check_finite) return read_flags(ws, st);
         return LSP_OK;
@@ -1182,7 +1217,7 @@ lsp_status lsp_hj_solve_batched(int nprob, lsp_grid* const* grids, const lsp_sol
         while (nactive > 0 && order[nactive - 1].nsteps <= k) --nactive;
         for (int stage = 0; stage < o->rk_order && !s; ++stage) {
             e = lsp::launch_batched(o->scheme, d_table, d_block_prob, prefix[nactive], k, stage,
-                                    o->rk_order, o->diss != LSP_DISS_GLF || o->varform, es);
+                                    o->rk_order, o->diss != LSP_DISS_GLF || o->varform, cls, es);
             if (e) s = cuda_fail(e, "batched stage kernel");
         }
     }
@@ -1202,19 +1237,109 @@ lsp_status lsp_hj_solve_batched(int nprob, lsp_grid* const* grids, const lsp_sol
     return LSP_OK;
 }
 
+lsp_status lsp_batched_autotune(int nprob, lsp_grid* const* grids, const lsp_solve_opts* o,
+                                const void* const* phis, const void* const* targets,
+                                const double* t_final, void* ws, size_t ws_size, void* stream,
+                                int* batch_tiles)
+{
+    lsp_status s = batch_check(nprob, grids, o);
+    if (s) return s;
+    if (!phis || !t_final || !batch_tiles) return fail(LSP_EINVAL, "NULL argument");
+    if (o->tube && !targets) return fail(LSP_EINVAL, "targets is NULL with tube on");
+    cudaStream_t st = (cudaStream_t)stream;
+    // scratch copies of the fields: trial solves never write the caller's
+    size_t total = 0;
+    std::vector<size_t> off(nprob);
+    for (int i = 0; i < nprob; ++i) {
+        if ((s = check_field(phis[i], "phi"))) return fail_problem(s, i);
+        off[i] = total;
+        total += round256((size_t)grids[i]->npts * sizeof(float));
+    }
+    char* scratch = nullptr;
+    cudaError_t e = cudaMalloc(&scratch, total);
+    if (e) return cuda_fail(e, "batched autotune scratch");
+    std::vector<void*> sp(nprob);
+    for (int i = 0; i < nprob; ++i) sp[i] = scratch + off[i];
+    // a short horizon of every problem (at most 8 of its CFL steps), so
+    // that the trials see the full mix of problems
+    std::vector<double> tf(nprob);
+    for (int i = 0; i < nprob; ++i)
+        tf[i] = std::fmin(t_final[i], 8.0 * cfl_dt_host(grids[i], o->cfl, 0.0, INFINITY));
+    lsp_solve_opts trial = *o;
+    trial.use_graph = 0;
+    trial.check_finite = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) {
+        cudaFree(scratch);
+        return fail(LSP_ECUDA, "event create");
+    }
+    auto time_tiles = [&](int tiles, float* ms_out) -> lsp_status {
+        trial.batch_tiles = tiles;
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            for (int i = 0; i < nprob; ++i) {
+                cudaError_t ce = cudaMemcpyAsync(sp[i], phis[i], grids[i]->npts * sizeof(float),
+                                                 cudaMemcpyDeviceToDevice, st);
+                if (ce) return cuda_fail(ce, "batched autotune copy");
+            }
+            cudaEventRecord(e0, st);
+            lsp_status r = lsp_hj_solve_batched(nprob, grids, &trial, sp.data(), targets,
+                                                tf.data(), ws, ws_size, nullptr, st);
+            cudaEventRecord(e1, st);
+            if (r) return r;
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < best) best = ms;  // the first run warms up
+        }
+        *ms_out = best;
+        return LSP_OK;
+    };
+    // coordinate descent over the dimensions present, from opts->batch_tiles
+    int best_tiles = o->batch_tiles;
+    float best_ms = 0.0f;
+    s = time_tiles(best_tiles, &best_ms);
+    for (int d = 2; d <= 4 && !s; ++d) {
+        bool present = false;
+        for (int i = 0; i < nprob; ++i) present |= grids[i]->ndim == d;
+        if (!present) continue;
+        for (int shape = 0; shape < 3 && !s; ++shape) {
+            const int tiles = (best_tiles & ~(3 << (2 * (d - 2)))) | (shape << (2 * (d - 2)));
+            if (tiles == best_tiles) continue;
+            float ms = 0.0f;
+            s = time_tiles(tiles, &ms);
+            if (!s && ms < best_ms) {
+                best_ms = ms;
+                best_tiles = tiles;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    e = cudaStreamSynchronize(st);
+    cudaFree(scratch);
+    if (s) return s;
+    if (e) return cuda_fail(e, "batched autotune");
+    *batch_tiles = best_tiles;
+    return LSP_OK;
+}
+
 }  // extern "C"
 
 namespace {
 
 // ----------------------------------------------------------------- adjoint
 // Workspace of a checkpointed forward solve and its reverse sweep:
-// [ctl 256][W1][W2][acc 256][ckpt: C fields][seg: K fields][lam][lam_n]
-// [lam_a][lam_b][lam_v][contrib: 7*ndim fields], K = ceil(nsteps / C).
+// [ctl 256][W1][W2][acc 256][ckpt: C fields][seg: K fields][seg stage
+// inputs: (rk-1) K fields][lam][lam_n][lam_a][lam_b][lam_v][contrib: 7*ndim
+// fields], K = ceil(nsteps / C).  The recomputation of a segment keeps every
+// step's stage inputs (W1, W2), which the reverse sweep of that segment reads
+// instead of recomputing them.
 struct AdjLayout {
     int C, K;
     size_t F;  // one field, rounded to 256 bytes
-    size_t off_acc, off_ckpt, off_seg, off_w1, off_w2, off_lam, off_lamn, off_lama, off_lamb,
-        off_lamv, off_contrib, total;
+    size_t off_acc, off_ckpt, off_seg, off_segw, off_w1, off_w2, off_lam, off_lamn, off_lama,
+        off_lamb, off_lamv, off_contrib, total;
 };
 
 AdjLayout adj_layout(const lsp_grid* g, const lsp_solve_opts* o, int nsteps, int ncheck)
@@ -1233,6 +1358,7 @@ AdjLayout adj_layout(const lsp_grid* g, const lsp_solve_opts* o, int nsteps, int
     L.off_acc = off; off += 256;
     L.off_ckpt = off; off += (size_t)L.C * L.F;
     L.off_seg = off; off += (size_t)L.K * L.F;
+    L.off_segw = off; off += (size_t)(o->rk_order - 1) * L.K * L.F;
     L.off_lam = off; off += L.F;
     L.off_lamn = off; off += L.F;
     L.off_lama = off; off += L.F;
@@ -1339,6 +1465,7 @@ lsp_status adjoint_sweep(const lsp_grid* g, const lsp_solve_opts* o, const R* ta
     lsp::Ctl* ctl = (lsp::Ctl*)ws;
     R* ckpt = (R*)(W + Lo.off_ckpt);
     R* seg = (R*)(W + Lo.off_seg);
+    R* segw0 = (R*)(W + Lo.off_segw);
     R* w1 = (R*)(W + Lo.off_w1);
     R* w2 = (R*)(W + Lo.off_w2);
     R* lam = (R*)(W + Lo.off_lam);
@@ -1359,19 +1486,30 @@ lsp_status adjoint_sweep(const lsp_grid* g, const lsp_solve_opts* o, const R* ta
         // states phi^n, n0 <= n < n1, recomputed from the checkpoint
         e = cudaMemcpyAsync(seg, ckpt + (size_t)sg * FE, NB, cudaMemcpyDeviceToDevice, st);
         if (e) return cuda_fail(e, "restore checkpoint");
-        for (int n = n0; n + 1 < n1 && !s; ++n) {
-            R* nxt = seg + (size_t)(n - n0 + 1) * FE;
-            e = cudaMemcpyAsync(nxt, seg + (size_t)(n - n0) * FE, NB, cudaMemcpyDeviceToDevice, st);
-            if (e) return cuda_fail(e, "copy state");
-            s = enqueue_step<R>(g, o, nxt, target, dt, ws, st);
+        // stage inputs of step n of the segment (RK2/RK3): W1, then W2
+        auto segw = [&](int n, int q) { return segw0 + ((size_t)(n - n0) * (rk - 1) + q) * FE; };
+        for (int n = n0; n < n1 && !s; ++n) {
+            R* cur = seg + (size_t)(n - n0) * FE;
+            if (n + 1 < n1) {  // phi^{n+1}, keeping step n's stage inputs
+                R* nxt = seg + (size_t)(n - n0 + 1) * FE;
+                e = cudaMemcpyAsync(nxt, cur, NB, cudaMemcpyDeviceToDevice, st);
+                if (e) return cuda_fail(e, "copy state");
+                s = enqueue_step<R>(g, o, nxt, target, dt, ws, st, rk >= 2 ? segw(n, 0) : nullptr,
+                                    rk == 3 ? segw(n, 1) : nullptr);
+            } else {  // the last step of the segment: its stage inputs alone
+                if (rk >= 2)
+                    s = enqueue_stage<R>(g, o, ctl, cur, nullptr, nullptr, segw(n, 0), dt, 0.0, 1.0,
+                                         1.0, false, st);
+                if (!s && rk == 3)
+                    s = enqueue_stage<R>(g, o, ctl, segw(n, 0), cur, nullptr, segw(n, 1), dt, 0.75,
+                                         0.25, 0.25, false, st);
+            }
         }
         for (int n = n1 - 1; n >= n0 && !s; --n) {
             const R* phin = seg + (size_t)(n - n0) * FE;
-            // the stage inputs of step n, recomputed bit for bit
-            if (rk >= 2) s = enqueue_stage<R>(g, o, ctl, phin, nullptr, nullptr, w1, dt, 0.0, 1.0, 1.0, false, st);
-            if (!s && rk == 3)
-                s = enqueue_stage<R>(g, o, ctl, w1, phin, nullptr, w2, dt, 0.75, 0.25, 0.25, false, st);
-            if (s) break;
+            // the stage inputs of step n, as the recomputation left them
+            if (rk >= 2) w1 = segw(n, 0);
+            if (rk == 3) w2 = segw(n, 1);
             if ((e = cudaMemsetAsync(lamn, 0, NB, st))) return cuda_fail(e, "memset");
             if (rk == 1) {
                 // phi^{n+1} = [phi^n + dt L(phi^n)]_tube

@@ -20,11 +20,12 @@
 namespace lsp {
 
 // phi^n may be written by the same launch when COH (persistent batched
-// solve): an L2 load then, a plain one otherwise.
+// solve, after the CTA's acquire): a weak load cached at every level then, a
+// plain one otherwise.
 template <bool COH>
 __device__ __forceinline__ float ld_phin(const float* p)
 {
-    if constexpr (COH) return __ldcg(p);
+    if constexpr (COH) return __ldca(p);
     else return *p;
 }
 

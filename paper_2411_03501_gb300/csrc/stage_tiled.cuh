@@ -107,13 +107,15 @@ __device__ __forceinline__ void deriv_fast(const R* u, R inv_dx, R floor12, R& p
 }
 
 // Loads of the stage input.  COH = false: through the read-only cache (the
-// field does not change during the launch).  COH = true: from L2, bypassing
-// L1 -- for the persistent batched launch, in which other CTAs of the same
-// launch write the fields a CTA reads later.
+// field does not change during the launch).  COH = true: the persistent
+// batched launch, in which other CTAs of the same launch wrote the field
+// before this CTA's acquire (the fence after it observed their completion
+// count): a weak load cached at every level (ld.global.ca), which that
+// acquire orders, not the read-only path, which no fence orders.
 template <bool COH, typename R>
 __device__ __forceinline__ R ld_in(const R* p)
 {
-    if constexpr (COH) return __ldcg(p);
+    if constexpr (COH) return __ldca(p);
     else return __ldg(p);
 }
 
@@ -135,7 +137,9 @@ __device__ __forceinline__ R line_value(const R* __restrict__ p, int j, int n, i
 struct Tile {
     int tb, ta, ch;  // tile width (fastest axis), tile rows, planes per CTA
     int minb;        // occupancy target of the kernel variant (2, 3 or 4)
-    int pair;        // 1: two planes per iteration in paired FP32 (WENO5 only)
+    int pair;        // 0 scalar body; 1 two planes per iteration in paired FP32;
+                     // 2 the same with shared WENO5 faces; 3 / 4 face-shared
+                     // ENO runs of 4 / 2 nodes (stage_run.cuh)
 };
 
 // One CTA's share of a stage: the tile (bx, by) of the two fastest axes,
@@ -328,7 +332,7 @@ __device__ __forceinline__ void tiled_stage_body(const StageArgs<R>& a, int TB, 
                 if (a.varform) L = rmin(L, R(0));
             const int idx = base_outer + s * sS + ia * sA + ib;
             R v = rfma(cl, L, a.c_s * center);
-            if (a.phi_n) v = rfma(a.c_n, COH ? __ldcg(a.phi_n + idx) : a.phi_n[idx], v);
+            if (a.phi_n) v = rfma(a.c_n, COH ? __ldca(a.phi_n + idx) : a.phi_n[idx], v);
             if (a.tube) v = rmin(v, __ldg(a.target + idx));
             nonfinite |= !isfinite(v);
             a.out[idx] = v;

@@ -123,10 +123,20 @@ def check_fp32_solve(got, want, response, spec, factor=3.0, max_frac=0.05):
         noise_spread, per node);
       * on C, |got - want| <= factor x the oracle's own (dilated) response
         there, and C is at most max_frac of the nodes.
+    ENO2/ENO3 solves are a discontinuous function of the rounding (a stencil
+    choice near a tie can go either way in another precision, and the two
+    trajectories then differ by more than rounding): for them the end state
+    is held to max(1e-4 max|want|, factor x the largest response), and the
+    tests check every step of the trajectory against the oracle's step from
+    the same input instead (trajectory_check, near-tied choices apart).
     Returns {"err": max|got-want|/max|want|, "err_outside": the same off C,
     "frac_c": |C| / nodes}."""
     scale = float(np.abs(want).max())
     err = np.abs(got - want)
+    if spec["scheme"] in ("eno2", "eno3"):
+        bar = max(BAR * scale, factor * float(response.max()))
+        assert float(err.max()) <= bar, (float(err.max()) / scale, bar / scale)
+        return {"err": float(err.max()) / scale, "err_outside": None, "frac_c": None}
     mask, R = conditioning_mask(response, scale, spec, factor)
     frac = float(mask.mean())
     assert frac <= max_frac, f"ill-conditioned set covers {frac:.2%} of the nodes"
@@ -140,6 +150,23 @@ def check_fp32_solve(got, want, response, spec, factor=3.0, max_frac=0.05):
             f"max|dphi| on the ill-conditioned set exceeds {factor}x the oracle's response by "
             f"{over[mask].max():.3e} at {np.unravel_index(np.where(mask, over, -np.inf).argmax(), err.shape)}")
     return {"err": float(err.max()) / scale, "err_outside": out / scale, "frac_c": frac}
+
+
+def trajectory_check(spec, P, x, gt, g32, a, t_final, nsteps):
+    """Every step of the GPU trajectory against the oracle's step from the
+    same FP32 input (stage tolerance; near-tied ENO selections apart)."""
+    t = 0.0
+    for _ in range(nsteps):
+        dt = oracle.cfl_dt(spec, a, spec["cfl"], t, t_final)
+        before = x.double().cpu().numpy()
+        P.step(x, gt, t=t, dt=dt)
+        got_step = x.double().cpu().numpy()
+        want_step = oracle.step(spec, before, dt, spec["rk"], target=g32)
+        L, _ = oracle.rate(spec, before)
+        tol = spec["rk"] * dt * rate_tol(spec, before, L, a) + 8 * U32 * np.abs(before).max()
+        compare(got_step, want_step, tol,
+                step_flip_allowance(spec, before, dt, spec["rk"], a, tol))
+        t += dt
 
 
 def sign_ok(got, want, spec):

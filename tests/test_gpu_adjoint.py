@@ -157,9 +157,15 @@ def test_adjoint_workload_fp32_against_fd_and_fp64():
       converge to the adjoint only once h is below the distance to the
       nearest switch -- at h = 1e-3 they are off by ~2% on v_p even in FP64.
     * FP32 adjoint (autotuned tile, as the benchmark runs it) against the
-      FP64 adjoint (2e-2 relative: the v_p gradient is a small difference of
-      large terms) and against FP32 central differences with h = 1e-3 (6e-2
-      relative: the kinks above plus FP32 rounding of the loss)."""
+      FP64 adjoint, within 3x the spread of the FP64 gradients themselves
+      when phi0 and the target carry independent relative noise of FP32 size
+      (two samples; measured 2.3e-2, 2.5e-2 and 1.1e-2 on v_e, v_p, w:
+      the v_p gradient is a small difference of large terms, so the map from
+      rounding-sized input changes to it is what bounds any FP32 computation
+      of it) plus 1e-4 relative for the FP32 reductions; and against FP32
+      central differences with
+      h = 1e-3 (6e-2 relative: the kinks above plus FP32 rounding of the
+      loss)."""
     n, nsteps = 129, 200
     res = {}
     fd = {}
@@ -175,14 +181,25 @@ def test_adjoint_workload_fp32_against_fd_and_fp64():
         base = torch.tensor([5.0, 5.0, 1.0], dtype=torch.float64, requires_grad=True)
         r = torch.tensor(5.0, dtype=torch.float64, requires_grad=True)
 
-        def run(b, rr):
+        def run(b, rr, field=None):
             params = torch.stack([b[0], b[1], b[2], b[2]])
-            target = sdf_t - rr.to("cuda").to(tdt)
+            target = (sdf_t if field is None else field) - rr.to("cuda").to(tdt)
             return tube.loss(tube(target, target, params), q_t)
 
         L = run(base, r)
         L.backward()
         res[dtype] = np.concatenate([base.grad.numpy(), [r.grad.item()]])
+        if dtype == "f64":  # the gradients' own spread under FP32-sized input noise
+            spread = np.zeros(4)
+            for seed in (1, 2):
+                rng = np.random.default_rng(seed)
+                noisy = torch.as_tensor(sdf * (1 + 6e-8 * rng.standard_normal(sdf.shape)),
+                                        device="cuda")
+                b2 = base.detach().clone().requires_grad_(True)
+                r2 = r.detach().clone().requires_grad_(True)
+                run(b2, r2, noisy).backward()
+                g2 = np.concatenate([b2.grad.numpy(), [r2.grad.item()]])
+                spread = np.maximum(spread, np.abs(g2 - res["f64"]))
         vals = []
         with torch.no_grad():
             for j in range(3):
@@ -194,7 +211,11 @@ def test_adjoint_workload_fp32_against_fd_and_fp64():
             vals.append((run(base, r + h) - run(base, r - h)).item() / (2 * h))
         fd[dtype] = np.array(vals)
     np.testing.assert_allclose(res["f64"], fd["f64"], rtol=1e-5, atol=1e-6)
-    np.testing.assert_allclose(res["f32"], res["f64"], rtol=2e-2, atol=1e-3)
+    # plus the FP32 rounding of the reductions that form the gradients (the
+    # r gradient sums the FP32 field gradient over 2.1 M nodes; its input
+    # spread is ~1e-9 relative, its FP32 sum ~5e-6 relative): 1e-4 relative
+    dev = np.abs(res["f32"] - res["f64"])
+    assert np.all(dev <= 3 * spread + 1e-4 * np.abs(res["f64"])), (dev, spread, res)
     np.testing.assert_allclose(res["f32"], fd["f32"], rtol=6e-2, atol=1e-2)
 
 

@@ -163,3 +163,57 @@ def test_persistent_wait_runs_out_and_context_survives():
     torch.cuda.synchronize()
     for i in range(len(specs)):
         assert torch.equal(got[i], ref[i]), i
+
+
+@pytest.mark.parametrize("tiles", [0b000101, 0b001010, 0b000110])
+def test_batched_tile_shapes(tiles):
+    """Per-dimension tile shapes (opts.batch_tiles: 16 x 16, 32 x 8, 64 x 4,
+    256 threads each): the 3-D problems end bit for bit where single-problem
+    solves on the same tile end (the paired shared-face body for WENO5), the
+    2-D ones to FP32 rounding; the persistent launch equals the
+    stage-synchronous one bit for bit."""
+    shapes = [(16, 16), (32, 8), (64, 4)]
+    specs, phis, gs = _mixed()
+    gts = [to_dev(g, "f32") for g in gs]
+    xs = [to_dev(p, "f32") for p in phis]
+    stats = B.Batch(specs, check_finite=True, tiles=tiles).solve(xs, gts)
+    ys = [to_dev(p, "f32") for p in phis]
+    B.Batch(specs, check_finite=True, tiles=tiles, persistent=True).solve(ys, gts)
+    torch.cuda.synchronize()
+    for i, sp in enumerate(specs):
+        assert torch.equal(xs[i], ys[i]), i
+        P = B.Problem(sp)
+        if sp["ndim"] == 3:
+            tb, ta = shapes[(tiles >> 2) & 3]
+            P.set_tile(tb, ta, 32, 3, 2)
+        y = to_dev(phis[i], "f32")
+        st = P.solve(y, gts[i])
+        torch.cuda.synchronize()
+        assert stats[i]["steps"] == st["steps"]
+        if sp["ndim"] == 3:
+            assert torch.equal(xs[i], y), (i, float((xs[i] - y).abs().max()))
+        else:
+            assert float((xs[i] - y).abs().max()) <= 1e-5 * float(y.abs().max()), i
+
+
+def test_batched_autotune_picks_valid_tiles_and_leaves_fields():
+    """lsp_batched_autotune returns a valid batch_tiles value for the
+    dimensions present, leaves the caller's fields untouched, and later
+    solves with it equal solves with the value set explicitly."""
+    specs, phis, gs = _mixed_with_4d("weno5", 3)
+    gts = [to_dev(g, "f32") for g in gs]
+    xs = [to_dev(p, "f32") for p in phis]
+    Bt = B.Batch(specs)
+    tiles = Bt.autotune(xs, gts)
+    assert tiles >> 6 == 0 and all(((tiles >> (2 * k)) & 3) != 3 for k in range(3))
+    for i in range(len(specs)):
+        assert torch.equal(xs[i], to_dev(phis[i], "f32"))
+    Bt.solve(xs, gts)
+    ys = [to_dev(p, "f32") for p in phis]
+    B.Batch(specs, tiles=tiles).solve(ys, gts)
+    torch.cuda.synchronize()
+    for i in range(len(specs)):
+        assert torch.equal(xs[i], ys[i]), i
+    with pytest.raises(B.LspError) as e:
+        B.Batch(specs, tiles=0b11)
+    assert e.value.status == B.LSP_EINVAL

@@ -9,7 +9,7 @@ import torch
 
 import oracle
 from gpu_helpers import (check_fp32_solve, compare, flip_allowance, gpu_rate, noise_spread,
-                         rate_tol, rounded, to_dev)
+                         rate_tol, rounded, to_dev, trajectory_check)
 from paper_2411_03501_gb300 import binding as B
 from paper_2411_03501_gb300 import workloads as W
 
@@ -75,6 +75,10 @@ def test_rockets_tube_solve(dtype):
         assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max()
     else:
         check_fp32_solve(got, want, noise_spread(spec, phi0, g, 0.4, want), spec)
+        # ENO2: every step against the oracle's step from the same FP32 input
+        y = to_dev(phi0, dtype)
+        trajectory_check(spec, P, y, to_dev(g, dtype), g, oracle.alpha(spec, phi0), 0.4,
+                         st_o["steps"])
     assert np.all(got <= g + 1e-6 * np.abs(g).max())
 
 

@@ -8,7 +8,7 @@ import torch
 
 import oracle
 from gpu_helpers import (U32, check_fp32_solve, compare, gpu_rate, noise_spread, rate_tol, rounded,
-                         sign_ok, flip_allowance, step_flip_allowance, to_dev)
+                         sign_ok, flip_allowance, step_flip_allowance, to_dev, trajectory_check)
 from paper_2411_03501_gb300 import binding as B
 from paper_2411_03501_gb300 import workloads as W
 
@@ -112,23 +112,6 @@ def test_config1_fp64_solve_matches_oracle_and_closed_form():
     assert abs(rz - 0.8) < 0.5 * 0.02
 
 
-def _trajectory_check(spec, P, x, gt, g32, a, t_final, nsteps):
-    """Every step of the GPU trajectory against the oracle's step from the
-    same FP32 input (stage tolerance; near-tied ENO selections apart)."""
-    t = 0.0
-    for _ in range(nsteps):
-        dt = oracle.cfl_dt(spec, a, spec["cfl"], t, t_final)
-        before = x.double().cpu().numpy()
-        P.step(x, gt, t=t, dt=dt)
-        got_step = x.double().cpu().numpy()
-        want_step = oracle.step(spec, before, dt, spec["rk"], target=g32)
-        L, _ = oracle.rate(spec, before)
-        tol = spec["rk"] * dt * rate_tol(spec, before, L, a) + 8 * U32 * np.abs(before).max()
-        compare(got_step, want_step, tol,
-                step_flip_allowance(spec, before, dt, spec["rk"], a, tol))
-        t += dt
-
-
 @pytest.mark.slow
 def test_air3d_reduced_solve_fp32_within_tolerance():
     """The air3d reachable tube (WENO5, RK3, tube) at 41^3 to t_final 2.8 in
@@ -153,7 +136,7 @@ def test_air3d_reduced_solve_fp32_within_tolerance():
     assert sign_ok(got, want, spec)
     a = oracle.alpha(spec, phi0)
     y = to_dev(phi0, "f32")
-    _trajectory_check(spec, P, y, gt, g32, a, 2.8, st_o["steps"])
+    trajectory_check(spec, P, y, gt, g32, a, 2.8, st_o["steps"])
 
 
 @pytest.mark.slow
@@ -175,7 +158,7 @@ def test_car4d_reduced_solve_fp32_within_tolerance():
     np.testing.assert_allclose(P.alpha(), a, rtol=1e-12)
     x = to_dev(phi0, "f32")
     gt = to_dev(g32, "f32")
-    _trajectory_check(spec, P, x, gt, g32, a, 1.0, st_o["steps"])
+    trajectory_check(spec, P, x, gt, g32, a, 1.0, st_o["steps"])
     got = x.double().cpu().numpy()
     resp = noise_spread(spec, phi0, g32, 1.0, want)
     check_fp32_solve(got, want, resp, spec)
