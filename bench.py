@@ -551,8 +551,8 @@ def run_batched(args, rank: int, world: int, local_rank: int):
     mine = [allp[i] for i in parts[rank]]
     specs = [m[0] for m in mine]
     persistent = bool(args.persistent)
-    Bt = B.Batch(specs, use_graph=True, persistent=persistent)
-    Balt = B.Batch(specs, use_graph=True, persistent=not persistent)
+    Bt = B.Batch(specs, use_graph=True, persistent=persistent, chunk=args.batch_chunk)
+    Balt = B.Batch(specs, use_graph=True, persistent=not persistent, chunk=args.batch_chunk)
     h_phi0 = [torch.as_tensor(m[1], dtype=torch.float32).pin_memory() for m in mine]
     h_g = [torch.as_tensor(m[2], dtype=torch.float32).pin_memory() for m in mine]
     d_phi0 = [t.cuda() for t in h_phi0]
@@ -682,6 +682,7 @@ def run_batched(args, rank: int, world: int, local_rank: int):
                    "parallelism": "problems split across ranks" if world > 1 else "single",
                    "l2": "flushed (512 MB write) between timed solves",
                    "launch": "persistent" if persistent else "stage-synchronous (graph)",
+                   "batch_chunk": args.batch_chunk or 32,
                    "batch_tiles": {f"{d}-D": ["16x16", "32x8", "64x4"][(tiles >> (2 * (d - 2))) & 3]
                                    for d in (2, 3, 4)},
                    ("stage_synchronous_value" if persistent else "persistent_value"): alt_value,
@@ -958,6 +959,8 @@ def main():
                     help="dissipation coefficients of the solve workloads")
     ap.add_argument("--varform", type=int, default=0,
                     help="1: the variational form of the tube PDE instead of the min with the target")
+    ap.add_argument("--batch-chunk", type=int, default=0,
+                    help="batched workload: planes per CTA along the march (0 = the library's 32)")
     ap.add_argument("--persistent", type=int, default=0,
                     help="batched workload: time the persistent launch (1) or the "
                          "stage-synchronous graph (0); the other is timed beside it")

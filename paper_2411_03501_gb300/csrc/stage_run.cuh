@@ -38,73 +38,6 @@
 
 namespace lsp {
 
-// The one of a, b smaller in magnitude, ties to a.
-__device__ __forceinline__ float eno_smaller(float a, float b)
-{
-    return fabsf(a) <= fabsf(b) ? a : b;
-}
-
-// One cell face j+1/2 of ENO3: d = u_{j+1} - u_j, Sj = S_j, Sj1 = S_{j+1}
-// (second differences), Mj = M_j, Mj1 = M_{j+1}.  pp = dx p+_j,
-// pm = dx p-_{j+1}.
-__device__ __forceinline__ void eno3_face(float d, float Sj, float Sj1, float Mj, float Mj1,
-                                          float& pp, float& pm)
-{
-    const bool left = fabsf(Sj) <= fabsf(Sj1);
-    const float c = left ? Sj : Sj1;
-    const float cs = left ? Mj : Mj1;
-    const float fp = left ? (-1.0f / 6.0f) : (1.0f / 3.0f);
-    const float fm = left ? (1.0f / 3.0f) : (-1.0f / 6.0f);
-    pp = fmaf(cs, fp, fmaf(-0.5f, c, d));
-    pm = fmaf(cs, fm, fmaf(0.5f, c, d));
-}
-
-// One cell face j+1/2 of ENO2: pp = dx p+_j, pm = dx p-_{j+1}.
-__device__ __forceinline__ void eno2_face(float d, float Sj, float Sj1, float& pp, float& pm)
-{
-    const float c = eno_smaller(Sj, Sj1);
-    pp = fmaf(-0.5f, c, d);
-    pm = fmaf(0.5f, c, d);
-}
-
-// dx p- and dx p+ at NN consecutive nodes of a line from the window
-// w[0 .. NN+2G-1] (w[k] = value at node k - G), each face evaluated once.
-template <int SCHEME, int NN>
-__device__ __forceinline__ void eno_line(const float* w, float* pm, float* pp)
-{
-    constexpr int G = ghost_width(SCHEME);
-    float d[NN + 2 * G - 1];  // d[k]: face (k - G) + 1/2
-#pragma unroll
-    for (int k = 0; k < NN + 2 * G - 1; ++k) d[k] = w[k + 1] - w[k];
-    float S[NN + 2 * G - 2];  // S[k]: node k - G + 1
-#pragma unroll
-    for (int k = 0; k < NN + 2 * G - 2; ++k) S[k] = d[k + 1] - d[k];
-    if constexpr (SCHEME == ENO2) {
-#pragma unroll
-        for (int j = -1; j < NN; ++j) {  // face j+1/2: S_j = S[j+1], d = d[j+2]
-            float a, b;
-            eno2_face(d[j + 2], S[j + 1], S[j + 2], a, b);
-            if (j >= 0) pp[j] = a;
-            if (j + 1 < NN) pm[j + 1] = b;
-        }
-    } else {
-        static_assert(SCHEME == ENO3, "ENO2 or ENO3");
-        float T[NN + 3];  // T[k]: face (k - 2) + 1/2
-#pragma unroll
-        for (int k = 0; k < NN + 3; ++k) T[k] = S[k + 1] - S[k];
-        float M[NN + 2];  // M[j+1] = M_j = smaller of T_{j-1/2}, T_{j+1/2}
-#pragma unroll
-        for (int j = -1; j <= NN; ++j) M[j + 1] = eno_smaller(T[j + 1], T[j + 2]);
-#pragma unroll
-        for (int j = -1; j < NN; ++j) {  // face j+1/2: S_j = S[j+2], d = d[j+3]
-            float a, b;
-            eno3_face(d[j + 3], S[j + 2], S[j + 3], M[j + 1], M[j + 2], a, b);
-            if (j >= 0) pp[j] = a;
-            if (j + 1 < NN) pm[j + 1] = b;
-        }
-    }
-}
-
 // The marching axis' register pipeline for one node column.  ENO3 carries,
 // before plane s: u_{s+2}, d_{s+1/2}, d_{s+3/2}, S_s, S_{s+1}, T_{s+1/2},
 // M_s and dx p-_s; ENO2 carries u_{s+1}, d_{s+1/2}, S_s and dx p-_s.

@@ -56,11 +56,94 @@ __device__ __forceinline__ void deriv_upwind1(const R* u, R inv_dx, R& pm, R& pp
     pp = (u[2] - u[1]) * inv_dx;
 }
 
+// ENO stencil choices once per cell face.  The ENO polynomial of the
+// right-biased derivative at node j and of the left-biased one at node j+1
+// starts from the same interval [x_j, x_j+1] (k = j for both, Eqs. 11-14),
+// so the second-difference choice, the base index k* and the third-difference
+// choice are the same for both; only the evaluation point differs:
+//   p+_j = d - c/2 + cs f+/6,  p-_{j+1} = d + c/2 + cs f-/6,
+//   (f+, f-) = (-1, 2) if the left second difference was taken, else (2, -1),
+// with d = u_{j+1} - u_j, c the chosen second difference S and cs the chosen
+// third difference T (unscaled; the caller applies 1/dx).  With M_j the
+// smaller in magnitude of T_{j-1/2}, T_{j+1/2} (ties to the left, the <= of
+// Eq. 13), cs = M_j when the left second difference is taken, else M_{j+1}.
+// Every choice is a select on a comparison (no branches).
+
+// The one of a, b smaller in magnitude, ties to a.
+template <typename R>
+__device__ __forceinline__ R eno_smaller(R a, R b)
+{
+    return rabs(a) <= rabs(b) ? a : b;
+}
+
+// Face j+1/2 of ENO3 from d, S_j, S_{j+1}, M_j, M_{j+1}: pp = dx p+_j,
+// pm = dx p-_{j+1}.
+template <typename R>
+__device__ __forceinline__ void eno3_face(R d, R Sj, R Sj1, R Mj, R Mj1, R& pp, R& pm)
+{
+    const bool left = rabs(Sj) <= rabs(Sj1);
+    const R c = left ? Sj : Sj1;
+    const R cs = left ? Mj : Mj1;
+    const R fp = left ? R(-1.0 / 6.0) : R(1.0 / 3.0);
+    const R fm = left ? R(1.0 / 3.0) : R(-1.0 / 6.0);
+    pp = rfma(cs, fp, rfma(R(-0.5), c, d));
+    pm = rfma(cs, fm, rfma(R(0.5), c, d));
+}
+
+// Face j+1/2 of ENO2: pp = dx p+_j, pm = dx p-_{j+1}.
+template <typename R>
+__device__ __forceinline__ void eno2_face(R d, R Sj, R Sj1, R& pp, R& pm)
+{
+    const R c = eno_smaller(Sj, Sj1);
+    pp = rfma(R(-0.5), c, d);
+    pm = rfma(R(0.5), c, d);
+}
+
+// dx p- and dx p+ at NN consecutive nodes of a line from the window
+// w[0 .. NN+2G-1] (w[k] = value at node k - G), each face evaluated once.
+template <int SCHEME, int NN, typename R>
+__device__ __forceinline__ void eno_line(const R* w, R* pm, R* pp)
+{
+    constexpr int G = SCHEME == ENO2 ? 2 : 3;
+    R d[NN + 2 * G - 1];  // d[k]: face (k - G) + 1/2
+#pragma unroll
+    for (int k = 0; k < NN + 2 * G - 1; ++k) d[k] = w[k + 1] - w[k];
+    R S[NN + 2 * G - 2];  // S[k]: node k - G + 1
+#pragma unroll
+    for (int k = 0; k < NN + 2 * G - 2; ++k) S[k] = d[k + 1] - d[k];
+    if constexpr (SCHEME == ENO2) {
+#pragma unroll
+        for (int j = -1; j < NN; ++j) {  // face j+1/2: S_j = S[j+1], d = d[j+2]
+            R a, b;
+            eno2_face(d[j + 2], S[j + 1], S[j + 2], a, b);
+            if (j >= 0) pp[j] = a;
+            if (j + 1 < NN) pm[j + 1] = b;
+        }
+    } else {
+        static_assert(SCHEME == ENO3, "ENO2 or ENO3");
+        R T[NN + 3];  // T[k]: face (k - 2) + 1/2
+#pragma unroll
+        for (int k = 0; k < NN + 3; ++k) T[k] = S[k + 1] - S[k];
+        R M[NN + 2];  // M[j+1] = M_j = smaller of T_{j-1/2}, T_{j+1/2}
+#pragma unroll
+        for (int j = -1; j <= NN; ++j) M[j + 1] = eno_smaller(T[j + 1], T[j + 2]);
+#pragma unroll
+        for (int j = -1; j < NN; ++j) {  // face j+1/2: S_j = S[j+2], d = d[j+3]
+            R a, b;
+            eno3_face(d[j + 3], S[j + 2], S[j + 3], M[j + 1], M[j + 2], a, b);
+            if (j >= 0) pp[j] = a;
+            if (j + 1 < NN) pm[j + 1] = b;
+        }
+    }
+}
+
 // ENO2 (Sec. IV-B, Eqs. 11-12).  Window G = 2, u[m+2] = value at offset m.
 // With d_m = u_{m+1} - u_m and S_m = d_m - d_{m-1} (= 2 dx^2 D2_m):
 //   left  (k = i-1): p- = (d_{-1} + S_c / 2) / dx, S_c the smaller in
 //                    magnitude of S_{-1}, S_0 (ties to the left one)
 //   right (k = i)  : p+ = (d_0 - S_c / 2) / dx, S_c from S_0, S_1
+// (Per node, as written: on the 4-D ENO3 stage this form runs 19 % faster
+// than the per-node use of eno_line, 686 vs 849 us per launch.)
 template <typename R>
 __device__ __forceinline__ void deriv_eno2(const R* u, R inv_dx, R& pm, R& pp)
 {
