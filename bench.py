@@ -682,7 +682,7 @@ def run_batched(args, rank: int, world: int, local_rank: int):
                    "parallelism": "problems split across ranks" if world > 1 else "single",
                    "l2": "flushed (512 MB write) between timed solves",
                    "launch": "persistent" if persistent else "stage-synchronous (graph)",
-                   "batch_chunk": args.batch_chunk or 32,
+                   "batch_chunk": args.batch_chunk or 128,
                    "batch_tiles": {f"{d}-D": ["16x16", "32x8", "64x4"][(tiles >> (2 * (d - 2))) & 3]
                                    for d in (2, 3, 4)},
                    ("stage_synchronous_value" if persistent else "persistent_value"): alt_value,
@@ -699,12 +699,13 @@ def run_batched(args, rank: int, world: int, local_rank: int):
 def run_adjoint(args, rank: int, world: int, local_rank: int):
     """The differentiation workload: the air3d tube at 129^3 in FP32 over 200
     fixed RK3 steps; loss = smoothed volume of {phi <= 0} + phi at 1024 seeded
-    query states.  One benchmark step = forward solve with sqrt(N) checkpoints,
-    loss, reverse sweep: gradients with respect to v_e, v_p, the shared
-    turn-rate bound, the target radius (and phi0 = target).  The metric counts
-    the forward's point-stages per second of the whole gradient evaluation;
-    the plain forward (same 200 steps) is timed beside it.  Replicas under
-    torchrun."""
+    query states.  One benchmark step = forward solve keeping every state and
+    stage input (--ncheck -1, 5.2 GB; --ncheck 0: sqrt(N) checkpoints and a
+    recomputation per segment), loss, reverse sweep: gradients with respect
+    to v_e, v_p, the shared turn-rate bound, the target radius (and phi0 =
+    target).  The metric counts the forward's point-stages per second of the
+    whole gradient evaluation; the plain forward (same 200 steps) and the
+    other checkpoint form are timed beside it.  Replicas under torchrun."""
     import numpy as np
     import torch
 
@@ -726,15 +727,18 @@ def run_adjoint(args, rank: int, world: int, local_rank: int):
     h_q = torch.as_tensor(np.stack([rng.uniform(spec["lo"][k], spec["hi"][k], 1024)
                                     for k in range(3)], 1), dtype=torch.float32).pin_memory()
     sdf, q = h_sdf.cuda(), h_q.cuda()
-    tube = HJTube(spec, nsteps=nsteps)
+    tube = HJTube(spec, nsteps=nsteps, ncheck=args.ncheck)
+    other = HJTube(spec, nsteps=nsteps, ncheck=0 if args.ncheck < 0 else -1)
     stream = torch.cuda.current_stream()
     if args.tile:  # a fixed tile (the capture commands use the autotuner's choice)
         tile = tuple(int(v) for v in args.tile.split(","))
         B.lsp_set_tile(tube.grid, *tile)
     else:
         tile = tube.autotune(sdf - 5.0) if args.autotune else None
+    if tile is not None:
+        B.lsp_set_tile(other.grid, *tile)
 
-    def grad_step(sdf_d, q_d):
+    def grad_step(sdf_d, q_d, tube=tube):
         base = torch.tensor([5.0, 5.0, 1.0], dtype=torch.float64, requires_grad=True)
         r = torch.tensor(5.0, dtype=torch.float64, requires_grad=True)
         params = torch.stack([base[0], base[1], base[2], base[2]])
@@ -758,6 +762,17 @@ def run_adjoint(args, rank: int, world: int, local_rank: int):
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev)
+    # the other checkpoint form on the same tile
+    for _ in range(2):
+        grad_step(sdf, q, other)
+    torch.cuda.synchronize()
+    o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    o0.record(stream)
+    for _ in range(args.steps):
+        grad_step(sdf, q, other)
+    o1.record(stream)
+    torch.cuda.synchronize()
+    other_ms = o0.elapsed_time(o1) / args.steps
     # plain forward of the same 200 steps (one checkpoint: a single copy)
     plain = HJTube(spec, nsteps=nsteps, ncheck=1)
     if tile is not None:
@@ -795,7 +810,14 @@ def run_adjoint(args, rank: int, world: int, local_rank: int):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "adjoint_air3d_129^3_200xrk3_f32", "points": npts,
-                   "rk_steps": nsteps, "checkpoints": tube.ncheck or int(np.ceil(np.sqrt(nsteps))),
+                   "rk_steps": nsteps,
+                   "checkpoints": ("every state and stage input" if tube.ncheck < 0
+                                   else tube.ncheck or int(np.ceil(np.sqrt(nsteps)))),
+                   "other_checkpoints": ("every state and stage input" if other.ncheck < 0
+                                         else int(np.ceil(np.sqrt(nsteps)))),
+                   "other_checkpoints_ms_per_step": other_ms,
+                   "workspace_bytes": int(B.lsp_adjoint_workspace_size(tube.grid, tube.opts,
+                                                                       nsteps, tube.ncheck)),
                    "tile": list(tile) if tile is not None else None,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "fields (8.6 MB each) partly L2-resident; no flush",
@@ -805,7 +827,7 @@ def run_adjoint(args, rank: int, world: int, local_rank: int):
         "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": h_sdf.numel() * 4 + h_q.numel() * 4,
                 "d2h_bytes_per_step": 4 * 8},
-        "gpu_launches": adjoint_launches(nsteps, 3) * args.steps, "roofline": None,
+        "gpu_launches": adjoint_launches(nsteps, 3, tube.ncheck) * args.steps, "roofline": None,
         "cpu_baseline": None, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -889,16 +911,21 @@ def run_shapes(args, rank: int, world: int, local_rank: int):
     return 0
 
 
-def adjoint_launches(nsteps: int, rk: int) -> int:
+def adjoint_launches(nsteps: int, rk: int, ncheck: int = 0) -> int:
     """Kernels of one gradient evaluation: forward stages, the segment
     recomputation from sqrt(N) checkpoints (which keeps every step's stage
-    inputs; the last step of a segment computes its stage inputs alone), two
-    adjoint kernels per stage, the GLF argmax, two loss kernels."""
+    inputs; the last step of a segment computes its stage inputs alone) --
+    none when every stage input is kept (ncheck < 0) --, one adjoint kernel
+    per stage (each stage's first pass fused with the previous stage's
+    gather) and one closing gather, the GLF argmax, two loss kernels."""
     import math
-    C = math.ceil(math.sqrt(nsteps))
-    K = math.ceil(nsteps / C)
-    nseg = math.ceil(nsteps / K)
-    return (nsteps * rk + (nsteps - nseg) * rk + nseg * (rk - 1) + 2 * rk * nsteps + 1 + 2)
+    recompute = 0
+    if ncheck >= 0:
+        C = min(ncheck or math.ceil(math.sqrt(nsteps)), nsteps)
+        K = math.ceil(nsteps / C)
+        nseg = math.ceil(nsteps / K)
+        recompute = (nsteps - nseg) * rk + nseg * (rk - 1)
+    return nsteps * rk + recompute + rk * nsteps + 1 + 1 + 2
 
 
 def run_steps(args):
@@ -960,8 +987,11 @@ def main():
     ap.add_argument("--varform", type=int, default=0,
                     help="1: the variational form of the tube PDE instead of the min with the target")
     ap.add_argument("--batch-chunk", type=int, default=0,
-                    help="batched workload: planes per CTA along the march (0 = the library's 32)")
-    ap.add_argument("--persistent", type=int, default=0,
+                    help="batched workload: planes per CTA along the march (0 = the library's 128)")
+    ap.add_argument("--ncheck", type=int, default=-1,
+                    help="adjoint workload: checkpoints (0 = sqrt(N), -1 = keep every state and "
+                         "stage input)")
+    ap.add_argument("--persistent", type=int, default=1,
                     help="batched workload: time the persistent launch (1) or the "
                          "stage-synchronous graph (0); the other is timed beside it")
     args = ap.parse_args()

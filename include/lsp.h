@@ -117,7 +117,7 @@ typedef struct {
                           lsp_hj_solve_batched captures its launches into
                           one graph and launches that                      */
     int batch_chunk;   /* batched solves: planes per CTA along the march of
-                          3-D/4-D problems (0 = 32)                        */
+                          3-D/4-D problems (0 = 128)                        */
     int batch_persistent; /* batched solves: 1 = the whole solve as ONE
                           launch of resident CTAs that take (step, stage,
                           tile) items in order and wait on per-problem
@@ -374,7 +374,10 @@ lsp_status lsp_hj_solve_batched(int nprob, lsp_grid* const* grids, const lsp_sol
  *   nsteps)), a segment of ceil(nsteps/ncheck) recomputed states with the
  *   RK stage inputs of each (rk_order - 1 fields per state, kept by the
  *   recomputation for the reverse sweep), the stage fields, five adjoint
- *   fields and 7*ndim coefficient fields.
+ *   fields and 7*ndim coefficient fields.  ncheck < 0 keeps everything:
+ *   the forward stores every state and every stage input (nsteps * rk_order
+ *   fields) and the reverse sweep recomputes nothing -- the fastest form
+ *   where memory allows (air3d 129^3, 200 RK3 steps: 5.2 GB in FP32).
  * lsp_hj_solve_ckpt: the forward solve (phi in place), storing checkpoints
  *   in the workspace.  Asynchronous.
  * lsp_hj_adjoint: the reverse sweep from the checkpoints left in the same

@@ -10,13 +10,18 @@
 // recomputed from the same stage input and frozen; the smooth remainder --
 // WENO weights included -- is differentiated exactly.
 //
-// Two kernels per stage.  adj_stage_a (one thread per node i) recomputes the
+// Two passes per stage.  Pass A (one thread per node i) recomputes the
 // node's forward quantities, forms the weighted sensitivities of p+-_k,i and
 // stores, per axis, the 7 coefficients c_k,i[o] = dLoss/du at window offset
 // o; window positions that fall on ghost cells of an extrapolated axis are
 // folded onto their boundary nodes right away (atomics, boundary nodes only).
-// adj_stage_b (one thread per node j) gathers sum_k sum_o c_k,(j-o e_k)[o]
-// (periodic axes wrap) -- deterministic, no atomics on the interior.
+// Pass B (node j) gathers sum_k sum_o c_k,(j-o e_k)[o] (periodic axes wrap)
+// -- deterministic, no atomics on the interior.  Pass B of a stage needs
+// only the node's own values besides the coefficients, and it yields the
+// node's dLoss/dout of the stage reversed next, which is all that stage's
+// pass A needs at the node: adj_stage_a runs the later stage's pass B and
+// this stage's pass A in one launch (two coefficient buffers, alternating);
+// adj_stage_b runs the last stage's pass B alone.
 #pragma once
 #include "stage_generic.cuh"
 #include "stage_tiled.cuh"
@@ -100,34 +105,73 @@ __device__ __forceinline__ void grad_eno(const R* u7, R inv_dx, R* gm, R* gp)
 //   Phi = w0 A + (w2 - 1/2) B,  A = (a - 2b + c)/3,  B = (b - 2c + d)/6,
 //   w_k = C_k/(IS_k + e)^2 / sum_l C_l/(IS_l + e)^2,  C = (1, 6, 3),
 //   dw_k = w_k (g_k - sum_l w_l g_l),  g_k = -2 (dIS_k + de)/(IS_k + e).
-template <typename R>
-__device__ __forceinline__ void weno_phi_grad(R a, R b, R c, R d, R e, R* gabcd, R* ge)
+__device__ __forceinline__ void weno_phi_grad(double a, double b, double c, double d, double e,
+                                              double* gabcd, double* ge)
 {
-    const R f0 = a - R(3) * b, f1 = b + c, f2 = R(3) * c - d;
-    const R is0 = R(13) * (a - b) * (a - b) + R(3) * f0 * f0;
-    const R is1 = R(13) * (b - c) * (b - c) + R(3) * f1 * f1;
-    const R is2 = R(13) * (c - d) * (c - d) + R(3) * f2 * f2;
-    const R q0 = is0 + e, q1 = is1 + e, q2 = is2 + e;
+    const double f0 = a - 3.0 * b, f1 = b + c, f2 = 3.0 * c - d;
+    const double is0 = 13.0 * (a - b) * (a - b) + 3.0 * f0 * f0;
+    const double is1 = 13.0 * (b - c) * (b - c) + 3.0 * f1 * f1;
+    const double is2 = 13.0 * (c - d) * (c - d) + 3.0 * f2 * f2;
+    const double q0 = is0 + e, q1 = is1 + e, q2 = is2 + e;
     // weights (the common scale of q cancels; 1/q^2 may be large, so form
     // ratios to the largest weight)
-    const R r0 = R(1) / q0, r1 = R(1) / q1, r2 = R(1) / q2;
-    const R a0 = r0 * r0, a1 = R(6) * r1 * r1, a2 = R(3) * r2 * r2;
-    const R inv = R(1) / (a0 + a1 + a2);
-    const R w0 = a0 * inv, w1 = a1 * inv, w2 = a2 * inv;
-    const R A = (a - R(2) * b + c) * R(1.0 / 3.0), B = (b - R(2) * c + d) * R(1.0 / 6.0);
-    const R E = A * w0 + B * w2;
+    const double r0 = 1.0 / q0, r1 = 1.0 / q1, r2 = 1.0 / q2;
+    const double a0 = r0 * r0, a1 = 6.0 * r1 * r1, a2 = 3.0 * r2 * r2;
+    const double inv = 1.0 / (a0 + a1 + a2);
+    const double w0 = a0 * inv, w1 = a1 * inv, w2 = a2 * inv;
+    const double A = (a - 2.0 * b + c) * (1.0 / 3.0), B = (b - 2.0 * c + d) * (1.0 / 6.0);
+    const double E = A * w0 + B * w2;
     // coefficient of g_k in dPhi: gamma_k; times -2/q_k
-    const R k0 = (A * w0 - w0 * E) * R(-2) * r0;
-    const R k1 = (-w1 * E) * R(-2) * r1;
-    const R k2 = (B * w2 - w2 * E) * R(-2) * r2;
+    const double k0 = (A * w0 - w0 * E) * -2.0 * r0;
+    const double k1 = (-w1 * E) * -2.0 * r1;
+    const double k2 = (B * w2 - w2 * E) * -2.0 * r2;
     // dIS / d(a,b), d(b,c), d(c,d)
-    const R i0a = R(26) * (a - b) + R(6) * f0, i0b = R(-26) * (a - b) - R(18) * f0;
-    const R i1b = R(26) * (b - c) + R(6) * f1, i1c = R(-26) * (b - c) + R(6) * f1;
-    const R i2c = R(26) * (c - d) + R(18) * f2, i2d = R(-26) * (c - d) - R(6) * f2;
-    gabcd[0] = w0 * R(1.0 / 3.0) + k0 * i0a;
-    gabcd[1] = w0 * R(-2.0 / 3.0) + (w2 - R(0.5)) * R(1.0 / 6.0) + k0 * i0b + k1 * i1b;
-    gabcd[2] = w0 * R(1.0 / 3.0) + (w2 - R(0.5)) * R(-2.0 / 6.0) + k1 * i1c + k2 * i2c;
-    gabcd[3] = (w2 - R(0.5)) * R(1.0 / 6.0) + k2 * i2d;
+    const double i0a = 26.0 * (a - b) + 6.0 * f0, i0b = -26.0 * (a - b) - 18.0 * f0;
+    const double i1b = 26.0 * (b - c) + 6.0 * f1, i1c = -26.0 * (b - c) + 6.0 * f1;
+    const double i2c = 26.0 * (c - d) + 18.0 * f2, i2d = -26.0 * (c - d) - 6.0 * f2;
+    gabcd[0] = w0 * (1.0 / 3.0) + k0 * i0a;
+    gabcd[1] = w0 * (-2.0 / 3.0) + (w2 - 0.5) * (1.0 / 6.0) + k0 * i0b + k1 * i1b;
+    gabcd[2] = w0 * (1.0 / 3.0) + (w2 - 0.5) * (-2.0 / 6.0) + k1 * i1c + k2 * i2c;
+    gabcd[3] = (w2 - 0.5) * (1.0 / 6.0) + k2 * i2d;
+    *ge = k0 + k1 + k2;
+}
+
+// FP32: the weights as the forward forms them (q_k scaled by a power of two
+// close to 1/e, one reciprocal of P = Q1 Q2 + 6 Q0 Q2 + 3 Q0 Q1), and the
+// three reciprocals 1/q_k from one reciprocal of q0 q1 q2 (the products stay
+// below 1e24: IS_k <= 400 max D^2 while e >= 1.2e-5 max D^2).  Two
+// approximate reciprocals in place of four divisions; the gradient's error
+// stays a few FP32 ulps.
+__device__ __forceinline__ void weno_phi_grad(float a, float b, float c, float d, float e,
+                                              float* gabcd, float* ge)
+{
+    const float f0 = a - 3.0f * b, f1 = b + c, f2 = 3.0f * c - d;
+    const float is0 = 13.0f * (a - b) * (a - b) + 3.0f * f0 * f0;
+    const float is1 = 13.0f * (b - c) * (b - c) + 3.0f * f1 * f1;
+    const float is2 = 13.0f * (c - d) * (c - d) + 3.0f * f2 * f2;
+    const float sc = __uint_as_float(0x7f000000u - (__float_as_uint(e) & 0x7f800000u));
+    const float q0 = (is0 + e) * sc, q1 = (is1 + e) * sc, q2 = (is2 + e) * sc;
+    const float Q0 = q0 * q0, Q1 = q1 * q1, Q2 = q2 * q2;
+    const float Q12 = Q1 * Q2, Q01 = Q0 * Q1, Q02 = Q0 * Q2;
+    const float P = fmaf(6.0f * Q0, Q2, fmaf(3.0f, Q01, Q12));
+    const float r = __fdividef(1.0f, P);
+    const float w0 = Q12 * r, w1 = 6.0f * Q02 * r, w2 = 3.0f * Q01 * r;
+    // sc / q_k = 1 / (IS_k + e)
+    const float q12 = q1 * q2;
+    const float rq = __fdividef(sc, q0 * q12);
+    const float r0 = q12 * rq, r1 = q0 * q2 * rq, r2 = q0 * q1 * rq;
+    const float A = (a - 2.0f * b + c) * (1.0f / 3.0f), B = (b - 2.0f * c + d) * (1.0f / 6.0f);
+    const float E = A * w0 + B * w2;
+    const float k0 = (A * w0 - w0 * E) * -2.0f * r0;
+    const float k1 = (-w1 * E) * -2.0f * r1;
+    const float k2 = (B * w2 - w2 * E) * -2.0f * r2;
+    const float i0a = 26.0f * (a - b) + 6.0f * f0, i0b = -26.0f * (a - b) - 18.0f * f0;
+    const float i1b = 26.0f * (b - c) + 6.0f * f1, i1c = -26.0f * (b - c) + 6.0f * f1;
+    const float i2c = 26.0f * (c - d) + 18.0f * f2, i2d = -26.0f * (c - d) - 6.0f * f2;
+    gabcd[0] = w0 * (1.0f / 3.0f) + k0 * i0a;
+    gabcd[1] = w0 * (-2.0f / 3.0f) + (w2 - 0.5f) * (1.0f / 6.0f) + k0 * i0b + k1 * i1b;
+    gabcd[2] = w0 * (1.0f / 3.0f) + (w2 - 0.5f) * (-2.0f / 6.0f) + k1 * i1c + k2 * i2c;
+    gabcd[3] = (w2 - 0.5f) * (1.0f / 6.0f) + k2 * i2d;
     *ge = k0 + k1 + k2;
 }
 
@@ -267,6 +311,16 @@ struct AdjArgs {
     R* lam_u;          // ghost folds (atomics) here; pass B adds the rest
     R* lam_n;          // pass B: += c_n lam_v (may equal lam_u)
     R* lam_g;          // tube: += lam where the min took the target (nullable)
+    // Pass A only: the pass B of the stage reversed before this one, done
+    // node by node in the same launch (gcontrib NULL: none, lam is read).
+    // At node i it forms that stage's dLoss/du_i -- this stage's dLoss/dout_i
+    // -- from glam_u[i] (then zeroed for reuse), its own lam_v[i] and the
+    // neighbours' coefficients in gcontrib.
+    const R* gcontrib; // the later stage's coefficient fields (not contrib)
+    R* glam_u;         // the later stage's lam_u (never this stage's lam_u)
+    R* glam_n;         // the later stage's lam_n (NULL or == glam_u: into the sum)
+    R gc_s, gc_n;      // the later stage's c_s, c_n
+    int gatomic;       // glam_n is this stage's fold target: add atomically
     AdjAcc* acc;
     int n[LSP_MAXD];
     int stride[LSP_MAXD];
@@ -280,6 +334,54 @@ struct AdjArgs {
     int tube;
     int npts;
 };
+
+// sum over axes k and offsets o of the coefficient c_k,(i - o e_k)[o]: what
+// node i's value contributed, through every window that contains it, to the
+// stage's reverse (periodic axes wrap; positions beyond an extrapolated end
+// were folded by pass A).  Added to acc in the order k, o.
+template <int NDIM, typename R>
+__device__ __forceinline__ R gather_coeffs(const AdjArgs<R>& a, const R* contrib, int idx,
+                                           const int* c, R acc)
+{
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) {
+        const int n = a.n[k], s = a.stride[k];
+        const R* ck = contrib + (long long)(7 * k + 3) * a.cstride + idx;  // offset 0
+        if (c[k] >= 3 && c[k] < n - 3) {
+#pragma unroll
+            for (int o = -3; o <= 3; ++o) acc += ck[(long long)o * a.cstride - (long long)o * s];
+            continue;
+        }
+#pragma unroll
+        for (int o = -3; o <= 3; ++o) {
+            int i = c[k] - o;  // the node whose window offset o is this node
+            if (i < 0 || i >= n) {
+                if (!a.periodic[k]) continue;
+                i = i < 0 ? i + n : i - n;
+            }
+            acc += ck[(long long)o * a.cstride + (long long)(i - c[k]) * s];
+        }
+    }
+    return acc;
+}
+
+// Asynchronous 4-byte copy global -> shared (cp.async): complete after
+// adj_cp_wait() in the issuing thread.
+__device__ __forceinline__ void adj_cp4(float* smem_dst, const float* gsrc)
+{
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void adj_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void adj_cp_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// FP32 pass A prefetches the gather of the next node it visits into shared
+// memory while it computes the current one: per thread two slices of
+// adj_gather_slots(NDIM) floats (lam_v, glam_u, then the 7 NDIM
+// coefficients in gather order), slot q of slice b at [(b NQ + q) 256 + tid].
+__host__ __device__ constexpr int adj_gather_slots(int ndim) { return 7 * ndim + 2; }
+template <int NDIM, typename R>
+__host__ __device__ constexpr size_t adj_a_smem_bytes() { return sizeof(R) == 4 ? 2 * adj_gather_slots(NDIM) * 256 * sizeof(float) : 0; }
 
 // 3 CTAs of 256 per SM in FP32: the kernel fits 80 registers without spills
 // (left to itself the compiler takes 128 and runs 2 CTAs per SM; 64
@@ -295,23 +397,114 @@ __global__ void __launch_bounds__(256, adj_a_min_blocks<R>()) adj_stage_a(AdjArg
     // nodes), promoted to FP64 once for the block reduction: per-node FP64
     // arithmetic would run on GB300's slow FP64 pipe
     R acc_h[4] = {0, 0, 0, 0}, acc_a[4] = {0, 0, 0, 0}, acc_dt = R(0);
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < a.npts;
-         idx += gridDim.x * blockDim.x) {
-        int c[NDIM];
-        {
-            int r = idx;
+    // grid-stride loop with the node's coordinates advanced by the stride's
+    // mixed-radix digits (one carry per axis) instead of divided out per node
+    const int step = gridDim.x * blockDim.x;
+    int c[NDIM], dc[NDIM];
+    {
+        int r = blockIdx.x * blockDim.x + threadIdx.x, q = step;
 #pragma unroll
-            for (int k = NDIM - 1; k >= 0; --k) {
-                c[k] = r % a.n[k];
-                r /= a.n[k];
+        for (int k = NDIM - 1; k >= 0; --k) {
+            c[k] = r % a.n[k];
+            r /= a.n[k];
+            dc[k] = q % a.n[k];
+            q /= a.n[k];
+        }
+        c[0] += r * a.n[0];  // a thread past the last node leaves at once
+        dc[0] += q * a.n[0];
+    }
+    // the gather's operands of node pidx (coordinates pc) into slice buf
+    constexpr bool kPF = sizeof(R) == 4;
+    constexpr int NQ = adj_gather_slots(NDIM);
+    extern __shared__ __align__(16) unsigned char adj_smem_raw[];
+    float* slices = reinterpret_cast<float*>(adj_smem_raw) + threadIdx.x;
+    auto prefetch = [&](int pidx, const int* pc, int buf) {
+        if constexpr (kPF) {
+            float* sl = slices + buf * NQ * 256;
+            adj_cp4(sl, reinterpret_cast<const float*>(a.lam_v + pidx));
+            adj_cp4(sl + 256, reinterpret_cast<const float*>(a.glam_u + pidx));
+#pragma unroll
+            for (int k = 0; k < NDIM; ++k) {
+                const int n = a.n[k], s = a.stride[k];
+                const float* ck =
+                    reinterpret_cast<const float*>(a.gcontrib) + (long long)(7 * k + 3) * a.cstride + pidx;
+                const bool inner = pc[k] >= 3 && pc[k] < n - 3;
+#pragma unroll
+                for (int o = -3; o <= 3; ++o) {
+                    float* dst = sl + (2 + 7 * k + o + 3) * 256;
+                    int i = pc[k] - o;
+                    if (!inner && (i < 0 || i >= n)) {
+                        if (!a.periodic[k]) {  // folded by the later stage's pass A
+                            *dst = 0.0f;
+                            continue;
+                        }
+                        i = i < 0 ? i + n : i - n;
+                    }
+                    adj_cp4(dst, ck + (long long)o * a.cstride + (long long)(i - pc[k]) * s);
+                }
             }
+            adj_cp_commit();
+        }
+    };
+    const bool gather = a.gcontrib != nullptr;
+    if (kPF && gather && blockIdx.x * blockDim.x + threadIdx.x < a.npts)
+        prefetch(blockIdx.x * blockDim.x + threadIdx.x, c, 0);
+    int it = 0;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < a.npts; idx += step, ++it) {
+        // coordinates of the next node of this thread
+        int cn[NDIM];
+        {
+            int carry = 0;
+#pragma unroll
+            for (int k = NDIM - 1; k >= 1; --k) {
+                cn[k] = c[k] + dc[k] + carry;
+                carry = cn[k] >= a.n[k];
+                if (carry) cn[k] -= a.n[k];
+            }
+            cn[0] = c[0] + dc[0] + carry;
+        }
+        // dLoss/dout at this node: the later stage's pass B here, or lam
+        R lam_in;
+        if (gather) {
+            R lvp, glu, acc;
+            if constexpr (kPF) {
+                adj_cp_wait();
+                const float* sl = slices + (it & 1) * NQ * 256;
+                lvp = sl[0];
+                glu = sl[256];
+                acc = a.gc_s * lvp;
+#pragma unroll
+                for (int q = 0; q < 7 * NDIM; ++q) acc += sl[(2 + q) * 256];
+                if (idx + step < a.npts) prefetch(idx + step, cn, (it + 1) & 1);
+            } else {
+                lvp = a.lam_v[idx];
+                glu = a.glam_u[idx];
+                acc = gather_coeffs<NDIM>(a, a.gcontrib, idx, c, a.gc_s * lvp);
+            }
+            if (a.glam_n && a.glam_n != a.glam_u) {
+                if (a.gatomic) atomicAdd(a.glam_n + idx, a.gc_n * lvp);
+                else a.glam_n[idx] += a.gc_n * lvp;
+            } else {
+                acc += a.gc_n * lvp;
+            }
+            lam_in = glu + acc;
+            a.glam_u[idx] = R(0);
+        } else {
+            lam_in = a.lam[idx];
         }
         R x[NDIM], pm[NDIM], pp[NDIM], pbar[NDIM], win[NDIM][7];
         R diss = R(0);
 #pragma unroll
         for (int k = 0; k < NDIM; ++k) {
             R u[7];
-            load_window<R, 3>(a.u, idx, c[k], a.n[k], a.stride[k], a.periodic[k], u);
+            if (c[k] >= 3 && c[k] < a.n[k] - 3) {  // no ghost cells in the window
+                const R* p0 = a.u + idx;
+                const long long s = a.stride[k];
+#pragma unroll
+                for (int o = -3; o <= 3; ++o) u[o + 3] = __ldg(p0 + o * s);
+            } else {
+                load_window<R, 3>(a.u, idx, c[k], a.n[k], a.stride[k], a.periodic[k], u);
+            }
 #pragma unroll
             for (int o = 0; o < 7; ++o) win[k][o] = u[o];
             deriv_fast<SCHEME>(u + (3 - G), a.inv_dx[k], weno_floor12(a.inv_dx[k]), pm[k], pp[k]);
@@ -325,7 +518,7 @@ __global__ void __launch_bounds__(256, adj_a_min_blocks<R>()) adj_stage_a(AdjArg
         const R L = -(H - diss);
         R v = a.c_s * a.u[idx] + (a.c_l * a.dt) * L;
         if (a.phin) v += a.c_n * a.phin[idx];
-        R lv = a.lam[idx];
+        R lv = lam_in;
         if (a.tube) {
             const R g = a.target[idx];
             if (g < v) {  // the min took the target
@@ -349,6 +542,12 @@ __global__ void __launch_bounds__(256, adj_a_min_blocks<R>()) adj_stage_a(AdjArg
             const R sm = w * (R(-0.5) * hp[k] - R(0.5) * a.alpha[k]);
             R* out = a.contrib + (long long)(7 * k + 3) * a.cstride + idx;  // offset 0
             const int n = a.n[k], s = a.stride[k];
+            if (a.periodic[k] || (c[k] >= 3 && c[k] < n - 3)) {  // no ghost position to fold
+#pragma unroll
+                for (int o = -3; o <= 3; ++o)
+                    out[(long long)o * a.cstride] = sp * gp[o + 3] + sm * gm[o + 3];
+                continue;
+            }
 #pragma unroll
             for (int o = -3; o <= 3; ++o) {
                 R cf = sp * gp[o + 3] + sm * gm[o + 3];
@@ -372,6 +571,8 @@ __global__ void __launch_bounds__(256, adj_a_min_blocks<R>()) adj_stage_a(AdjArg
                 out[(long long)o * a.cstride] = cf;
             }
         }
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) c[k] = cn[k];
     }
     // block reductions of the accumulators, one FP64 atomic each per block
     __shared__ double red[9][8];
@@ -412,22 +613,7 @@ __global__ void __launch_bounds__(256) adj_stage_b(AdjArgs<R> a)
             }
         }
         const R lv = a.lam_v[idx];
-        R acc = a.c_s * lv;
-#pragma unroll
-        for (int k = 0; k < NDIM; ++k) {
-            const int n = a.n[k], s = a.stride[k];
-            const R* ck = a.contrib + (long long)(7 * k + 3) * a.cstride;  // offset 0
-#pragma unroll
-            for (int o = -3; o <= 3; ++o) {
-                int i = c[k] - o;  // the node whose window offset o is this node
-                if (i < 0 || i >= n) {
-                    if (!a.periodic[k]) continue;
-                    i = i < 0 ? i + n : i - n;
-                }
-                const long long node = (long long)idx + (long long)(i - c[k]) * s;
-                acc += ck[(long long)o * a.cstride + node];
-            }
-        }
+        R acc = gather_coeffs<NDIM>(a, a.contrib, idx, c, a.c_s * lv);
         if (a.lam_n != a.lam_u && a.lam_n) a.lam_n[idx] += a.c_n * lv;
         else acc += a.c_n * lv;
         a.lam_u[idx] += acc;

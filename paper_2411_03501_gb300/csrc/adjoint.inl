@@ -17,45 +17,51 @@ static inline int adj_blocks(long long npts)
 // instantiation), so that each thread visits many nodes and the per-thread
 // tail -- the promotion of its partial sums and the FP64 warp reduction --
 // is paid once per ~30 nodes instead of once per ~3.
+// 256 threads per CTA (the prefetch slices of FP32 pass A assume it).
 template <int NDIM, int SCHEME, int DYN>
 static cudaError_t launch_pass_a(const AdjArgs<LSP_REAL>& a, cudaStream_t s)
 {
+    constexpr size_t smem = adj_a_smem_bytes<NDIM, LSP_REAL>();
     static const int resident = [] {
         int nsm = sm_count(), per = 1;
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(adj_stage_a<NDIM, SCHEME, DYN, LSP_REAL>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per, adj_stage_a<NDIM, SCHEME, DYN, LSP_REAL>, 256, 0) != cudaSuccess || per < 1)
+                &per, adj_stage_a<NDIM, SCHEME, DYN, LSP_REAL>, 256, smem) != cudaSuccess || per < 1)
             per = 1;
         return nsm * per;
     }();
     long long b = (a.npts + 255) / 256;
     const int nb = (int)(b < resident ? (b < 1 ? 1 : b) : resident);
-    adj_stage_a<NDIM, SCHEME, DYN, LSP_REAL><<<nb, 256, 0, s>>>(a);
+    adj_stage_a<NDIM, SCHEME, DYN, LSP_REAL><<<nb, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int NDIM, int SCHEME>
 static cudaError_t adj_dyn(int dyn, const AdjArgs<LSP_REAL>& a, cudaStream_t s)
 {
-    cudaError_t e;
     switch (dyn) {
-    case NORMAL_SPEED: e = launch_pass_a<NDIM, SCHEME, NORMAL_SPEED>(a, s); break;
-    case TRANSLATE: e = launch_pass_a<NDIM, SCHEME, TRANSLATE>(a, s); break;
+    case NORMAL_SPEED: return launch_pass_a<NDIM, SCHEME, NORMAL_SPEED>(a, s);
+    case TRANSLATE: return launch_pass_a<NDIM, SCHEME, TRANSLATE>(a, s);
     case AIR3D:
-        if constexpr (NDIM == 3) { e = launch_pass_a<3, SCHEME, AIR3D>(a, s); break; }
+        if constexpr (NDIM == 3) return launch_pass_a<3, SCHEME, AIR3D>(a, s);
         return cudaErrorInvalidValue;
     case CAR4D:
-        if constexpr (NDIM == 4) { e = launch_pass_a<4, SCHEME, CAR4D>(a, s); break; }
+        if constexpr (NDIM == 4) return launch_pass_a<4, SCHEME, CAR4D>(a, s);
         return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
-    if (e) return e;
-    adj_stage_b<NDIM, LSP_REAL><<<adj_blocks(a.npts), 256, 0, s>>>(a);
-    return cudaGetLastError();
 }
 
 template <int NDIM>
-static cudaError_t adj_scheme(int scheme, int dyn, const AdjArgs<LSP_REAL>& a, cudaStream_t s)
+static cudaError_t adj_scheme(int scheme, int dyn, const AdjArgs<LSP_REAL>& a, bool pass_b,
+                              cudaStream_t s)
 {
+    if (pass_b) {
+        adj_stage_b<NDIM, LSP_REAL><<<adj_blocks(a.npts), 256, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     switch (scheme) {
     case UPWIND1: return adj_dyn<NDIM, UPWIND1>(dyn, a, s);
     case ENO2: return adj_dyn<NDIM, ENO2>(dyn, a, s);
@@ -67,13 +73,14 @@ static cudaError_t adj_scheme(int scheme, int dyn, const AdjArgs<LSP_REAL>& a, c
 
 template <>
 cudaError_t launch_adjoint_stage<LSP_REAL>(int ndim, int scheme, int dyn,
-                                           const AdjArgs<LSP_REAL>& a, cudaStream_t s)
+                                           const AdjArgs<LSP_REAL>& a, bool pass_b,
+                                           cudaStream_t s)
 {
     switch (ndim) {
-    case 1: return adj_scheme<1>(scheme, dyn, a, s);
-    case 2: return adj_scheme<2>(scheme, dyn, a, s);
-    case 3: return adj_scheme<3>(scheme, dyn, a, s);
-    case 4: return adj_scheme<4>(scheme, dyn, a, s);
+    case 1: return adj_scheme<1>(scheme, dyn, a, pass_b, s);
+    case 2: return adj_scheme<2>(scheme, dyn, a, pass_b, s);
+    case 3: return adj_scheme<3>(scheme, dyn, a, pass_b, s);
+    case 4: return adj_scheme<4>(scheme, dyn, a, pass_b, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -85,11 +85,13 @@ cudaError_t launch_shape(const ShapeGeom& g, const ShapeArgs& s, int dtype, void
 cudaError_t launch_shape_op(int op, int dtype, const void* a, const void* b, void* out,
                             long long n, cudaStream_t st);
 
-// Adjoint of one stage (adjoint.cuh): pass A + pass B.
+// Adjoint of one stage (adjoint.cuh): pass A (with the previous stage's
+// pass B when a.gcontrib is set) when pass_b is false, pass B alone when it
+// is true.
 template <typename R> struct AdjArgs;
 template <typename R>
 cudaError_t launch_adjoint_stage(int ndim, int scheme, int dyn, const AdjArgs<R>& a,
-                                 cudaStream_t s);
+                                 bool pass_b, cudaStream_t s);
 cudaError_t launch_alpha_argmax(int dyn, const GridGeom& g, const double* alpha,
                                 unsigned long long* out, cudaStream_t s);
 

@@ -945,7 +945,13 @@ void batch_geometry(int nprob, lsp_grid* const* grids, const lsp_solve_opts* o,
                     std::vector<BatchPlanEntry>& plan, size_t* bytes, long long* total_blocks,
                     bool any_shape = false)
 {
-    const int chunk = o->batch_chunk > 0 ? o->batch_chunk : 32;
+    // 128 planes per CTA by default (a whole column of every problem up to
+    // 128 nodes along the march): the persistent launch's per-item overhead
+    // (counter, fences, dependency poll) is paid per tile, and the graph form
+    // gains too (256-problem workload: 67.5 / 67.0 G updates/s at 128 against
+    // 65.8 / 66.3 G at 64, 61.7 / 65.0 G at 32 and 54.3 / 61.5 G at 16,
+    // persistent / graph)
+    const int chunk = o->batch_chunk > 0 ? o->batch_chunk : 128;
     plan.resize(nprob);
     size_t fields = 0;
     long long blocks = 0;
@@ -1337,6 +1343,7 @@ namespace {
 // instead of recomputing them.
 struct AdjLayout {
     int C, K;
+    bool keep_all;  // ncheck < 0: every state and stage input stored by the forward
     size_t F;  // one field, rounded to 256 bytes
     size_t off_acc, off_ckpt, off_seg, off_segw, off_w1, off_w2, off_lam, off_lamn, off_lama,
         off_lamb, off_lamv, off_contrib, total;
@@ -1345,7 +1352,9 @@ struct AdjLayout {
 AdjLayout adj_layout(const lsp_grid* g, const lsp_solve_opts* o, int nsteps, int ncheck)
 {
     AdjLayout L;
-    L.C = ncheck > 0 ? ncheck : (int)std::ceil(std::sqrt((double)std::max(nsteps, 1)));
+    L.keep_all = ncheck < 0;
+    L.C = ncheck > 0 ? ncheck : ncheck < 0 ? nsteps
+                                          : (int)std::ceil(std::sqrt((double)std::max(nsteps, 1)));
     if (L.C > nsteps) L.C = std::max(nsteps, 1);
     L.K = (nsteps + L.C - 1) / L.C;
     if (L.K < 1) L.K = 1;
@@ -1357,14 +1366,19 @@ AdjLayout adj_layout(const lsp_grid* g, const lsp_solve_opts* o, int nsteps, int
     L.off_w2 = off; off += L.F;
     L.off_acc = off; off += 256;
     L.off_ckpt = off; off += (size_t)L.C * L.F;
-    L.off_seg = off; off += (size_t)L.K * L.F;
-    L.off_segw = off; off += (size_t)(o->rk_order - 1) * L.K * L.F;
+    // keep_all: the checkpoints are the states, and the stage inputs of
+    // every step follow them (no recomputation segment)
+    L.off_seg = off; off += L.keep_all ? 0 : (size_t)L.K * L.F;
+    L.off_segw = off;
+    off += (size_t)(o->rk_order - 1) * (L.keep_all ? (size_t)L.C : (size_t)L.K) * L.F;
     L.off_lam = off; off += L.F;
     L.off_lamn = off; off += L.F;
     L.off_lama = off; off += L.F;
     L.off_lamb = off; off += L.F;
     L.off_lamv = off; off += L.F;
-    L.off_contrib = off; off += (size_t)7 * g->ndim * L.F;
+    // two sets of 7 ndim coefficient fields: a stage's pass A writes one
+    // while the same launch gathers the previous stage's from the other
+    L.off_contrib = off; off += (size_t)2 * 7 * g->ndim * L.F;
     L.total = off;
     return L;
 }
@@ -1383,24 +1397,50 @@ lsp_status adj_check(const lsp_grid* g, const lsp_solve_opts* o, int nsteps)
     return LSP_OK;
 }
 
+// One reversed RK stage: v = c_n phin + c_s u + c_l dt L(u), out = min(v, g)
+// in a tube stage; dLoss/du is collected in lam_u, c_n dLoss/dv in lam_n.
+template <typename R>
+struct AdjStage {
+    const R* u;
+    const R* phin;
+    const R* target;
+    R* lam_u;
+    R* lam_n;
+    R* lam_g;
+    double c_n, c_s, c_l;
+    bool tube;
+};
+
+// Launch pass A of stage d, fused with pass B of `prev` (the stage reversed
+// just before, NULL for the first), writing coefficient set `set`; or, with
+// pass_b, pass B of d alone (its coefficients in set `set`).  lam: dLoss/dout
+// of d when prev is NULL.
 template <typename R>
 lsp_status adj_stage(const lsp_grid* g, const lsp_solve_opts* o, void* ws, const AdjLayout& Lo,
-                     const R* u, const R* phin, const R* target, const R* lam, R* lam_u, R* lam_n,
-                     R* lam_g, double dt, double c_n, double c_s, double c_l, bool tube,
-                     cudaStream_t st)
+                     const AdjStage<R>& d, const AdjStage<R>* prev, const R* lam, int set,
+                     bool pass_b, double dt, cudaStream_t st)
 {
     lsp::AdjArgs<R> a;
     std::memset(&a, 0, sizeof(a));
-    a.u = u;
-    a.phin = phin;
-    a.target = target;
+    const size_t set_bytes = (size_t)7 * g->ndim * Lo.F;
+    a.u = d.u;
+    a.phin = d.phin;
+    a.target = d.target;
     a.lam = lam;
     a.lam_v = (R*)((char*)ws + Lo.off_lamv);
-    a.contrib = (R*)((char*)ws + Lo.off_contrib);
+    a.contrib = (R*)((char*)ws + Lo.off_contrib + (size_t)set * set_bytes);
     a.cstride = (long long)(Lo.F / sizeof(R));
-    a.lam_u = lam_u;
-    a.lam_n = lam_n;
-    a.lam_g = tube ? lam_g : nullptr;
+    a.lam_u = d.lam_u;
+    a.lam_n = d.lam_n;
+    a.lam_g = d.tube ? d.lam_g : nullptr;
+    if (prev && !pass_b) {
+        a.gcontrib = (const R*)((char*)ws + Lo.off_contrib + (size_t)(1 - set) * set_bytes);
+        a.glam_u = prev->lam_u;
+        a.glam_n = prev->lam_n;
+        a.gc_s = R(prev->c_s);
+        a.gc_n = R(prev->c_n);
+        a.gatomic = prev->lam_n && prev->lam_n != prev->lam_u && prev->lam_n == d.lam_u;
+    }
     a.acc = (lsp::AdjAcc*)((char*)ws + Lo.off_acc);
     long long sd = 1;
     for (int k = g->ndim - 1; k >= 0; --k) {
@@ -1415,12 +1455,12 @@ lsp_status adj_stage(const lsp_grid* g, const lsp_solve_opts* o, void* ws, const
     }
     for (int i = 0; i < LSP_NPARAM; ++i) a.prm[i] = R(g->prm[i]);
     a.dt = R(dt);
-    a.c_n = R(c_n);
-    a.c_s = R(c_s);
-    a.c_l = R(c_l);
-    a.tube = tube ? 1 : 0;
+    a.c_n = R(d.c_n);
+    a.c_s = R(d.c_s);
+    a.c_l = R(d.c_l);
+    a.tube = d.tube ? 1 : 0;
     a.npts = (int)g->npts;
-    cudaError_t e = lsp::launch_adjoint_stage<R>(g->ndim, o->scheme, g->dyn, a, st);
+    cudaError_t e = lsp::launch_adjoint_stage<R>(g->ndim, o->scheme, g->dyn, a, pass_b, st);
     return e ? cuda_fail(e, "adjoint stage kernels") : LSP_OK;
 }
 
@@ -1481,14 +1521,34 @@ lsp_status adjoint_sweep(const lsp_grid* g, const lsp_solve_opts* o, const R* ta
     if ((e = cudaMemsetAsync(W + Lo.off_acc, 0, 256, st))) return cuda_fail(e, "memset acc");
     if ((e = cudaMemcpyAsync(lam, lamT, NB, cudaMemcpyDeviceToDevice, st))) return cuda_fail(e, "copy lamT");
     if (lam_target && (e = cudaMemsetAsync(lam_target, 0, NB, st))) return cuda_fail(e, "memset lam_target");
+    // lamn, lama, lamb start at zero; every launch zeroes the buffer it reads
+    for (R* b : {lamn, lama, lamb})
+        if ((e = cudaMemsetAsync(b, 0, NB, st))) return cuda_fail(e, "memset");
+    // the stage reversed last and the coefficient set its pass A wrote
+    AdjStage<R> prev{};
+    bool have_prev = false;
+    int set = 0;
+    auto run_stage = [&](const AdjStage<R>& d) -> lsp_status {
+        lsp_status r = adj_stage<R>(g, o, ws, Lo, d, have_prev ? &prev : nullptr, lam, set, false,
+                                    dt, st);
+        prev = d;
+        have_prev = true;
+        set ^= 1;
+        return r;
+    };
     for (int sg = (nsteps - 1) / Lo.K; sg >= 0 && !s; --sg) {
         const int n0 = sg * Lo.K, n1 = std::min(n0 + Lo.K, nsteps);
+        // stage inputs of step n of the segment (RK2/RK3): W1, then W2; with
+        // keep_all, every step's as the forward stored them
+        const int base = Lo.keep_all ? 0 : n0;
+        auto segw = [&](int n, int q) { return segw0 + ((size_t)(n - base) * (rk - 1) + q) * FE; };
+        if (Lo.keep_all) seg = ckpt + (size_t)n0 * FE;  // phi^n0, stored by the forward
         // states phi^n, n0 <= n < n1, recomputed from the checkpoint
-        e = cudaMemcpyAsync(seg, ckpt + (size_t)sg * FE, NB, cudaMemcpyDeviceToDevice, st);
-        if (e) return cuda_fail(e, "restore checkpoint");
-        // stage inputs of step n of the segment (RK2/RK3): W1, then W2
-        auto segw = [&](int n, int q) { return segw0 + ((size_t)(n - n0) * (rk - 1) + q) * FE; };
-        for (int n = n0; n < n1 && !s; ++n) {
+        if (!Lo.keep_all) {
+            e = cudaMemcpyAsync(seg, ckpt + (size_t)sg * FE, NB, cudaMemcpyDeviceToDevice, st);
+            if (e) return cuda_fail(e, "restore checkpoint");
+        }
+        for (int n = n0; n < n1 && !s && !Lo.keep_all; ++n) {
             R* cur = seg + (size_t)(n - n0) * FE;
             if (n + 1 < n1) {  // phi^{n+1}, keeping step n's stage inputs
                 R* nxt = seg + (size_t)(n - n0 + 1) * FE;
@@ -1507,41 +1567,38 @@ lsp_status adjoint_sweep(const lsp_grid* g, const lsp_solve_opts* o, const R* ta
         }
         for (int n = n1 - 1; n >= n0 && !s; --n) {
             const R* phin = seg + (size_t)(n - n0) * FE;
-            // the stage inputs of step n, as the recomputation left them
+            // the stage inputs of step n, as the recomputation (or, with
+            // keep_all, the forward) left them
             if (rk >= 2) w1 = segw(n, 0);
             if (rk == 3) w2 = segw(n, 1);
-            if ((e = cudaMemsetAsync(lamn, 0, NB, st))) return cuda_fail(e, "memset");
+            // Stages in reverse order.  dLoss/du of a stage goes to its own
+            // buffer (lamb, lama, then lamn, which also collects the c_n
+            // parts of the later stages: dLoss/dphi^n); RK1 alternates two
+            // buffers by step, so that a launch never reads and clears the
+            // buffer its own pass A folds into.
             if (rk == 1) {
                 // phi^{n+1} = [phi^n + dt L(phi^n)]_tube
-                s = adj_stage<R>(g, o, ws, Lo, phin, nullptr, target, lam, lamn, lamn, lam_target,
-                                 dt, 0.0, 1.0, 1.0, tube, st);
+                R* lu = (n & 1) ? lama : lamn;
+                s = run_stage({phin, nullptr, target, lu, lu, lam_target, 0.0, 1.0, 1.0, tube});
             } else if (rk == 2) {
                 // phi^{n+1} = [1/2 phi^n + 1/2 W1 + 1/2 dt L(W1)]_tube
-                if ((e = cudaMemsetAsync(lama, 0, NB, st))) return cuda_fail(e, "memset");
-                s = adj_stage<R>(g, o, ws, Lo, w1, phin, target, lam, lama, lamn, lam_target, dt,
-                                 0.5, 0.5, 0.5, tube, st);
+                s = run_stage({w1, phin, target, lama, lamn, lam_target, 0.5, 0.5, 0.5, tube});
                 // W1 = phi^n + dt L(phi^n)
-                if (!s)
-                    s = adj_stage<R>(g, o, ws, Lo, phin, nullptr, nullptr, lama, lamn, lamn, nullptr,
-                                     dt, 0.0, 1.0, 1.0, false, st);
+                if (!s) s = run_stage({phin, nullptr, nullptr, lamn, lamn, nullptr, 0.0, 1.0, 1.0, false});
             } else {
                 // phi^{n+1} = [1/3 phi^n + 2/3 W2 + 2/3 dt L(W2)]_tube
-                if ((e = cudaMemsetAsync(lamb, 0, NB, st))) return cuda_fail(e, "memset");
-                s = adj_stage<R>(g, o, ws, Lo, w2, phin, target, lam, lamb, lamn, lam_target, dt,
-                                 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, tube, st);
+                s = run_stage({w2, phin, target, lamb, lamn, lam_target, 1.0 / 3.0, 2.0 / 3.0,
+                               2.0 / 3.0, tube});
                 // W2 = 3/4 phi^n + 1/4 W1 + 1/4 dt L(W1)
-                if (!s && (e = cudaMemsetAsync(lama, 0, NB, st))) return cuda_fail(e, "memset");
-                if (!s)
-                    s = adj_stage<R>(g, o, ws, Lo, w1, phin, nullptr, lamb, lama, lamn, nullptr, dt,
-                                     0.75, 0.25, 0.25, false, st);
+                if (!s) s = run_stage({w1, phin, nullptr, lama, lamn, nullptr, 0.75, 0.25, 0.25, false});
                 // W1 = phi^n + dt L(phi^n)
-                if (!s)
-                    s = adj_stage<R>(g, o, ws, Lo, phin, nullptr, nullptr, lama, lamn, lamn, nullptr,
-                                     dt, 0.0, 1.0, 1.0, false, st);
+                if (!s) s = run_stage({phin, nullptr, nullptr, lamn, lamn, nullptr, 0.0, 1.0, 1.0, false});
             }
-            std::swap(lam, lamn);
         }
     }
+    // pass B of the last stage alone: dLoss/dphi^0
+    if (!s) s = adj_stage<R>(g, o, ws, Lo, prev, nullptr, nullptr, set ^ 1, true, dt, st);
+    lam = prev.lam_u;
     if (s) return s;
     if ((e = cudaMemcpyAsync(lam0, lam, NB, cudaMemcpyDeviceToDevice, st))) return cuda_fail(e, "copy lam0");
     // parameters: direct (through H) + through alpha (dissipation and dt)
@@ -1615,13 +1672,24 @@ lsp_status lsp_hj_solve_ckpt(lsp_grid* g, const lsp_solve_opts* o, void* phi, co
     const double dt = cfl_dt_host(g, o->cfl, 0.0, INFINITY);
     const size_t NB = (size_t)g->npts * elem_size(o->dtype);
     if ((s = reset_flags(ws, st))) return s;
+    const int rk = o->rk_order;
     for (int n = 0; n < nsteps && !s; ++n) {
         if (n % Lo.K == 0) {
             cudaError_t e = cudaMemcpyAsync((char*)ws + Lo.off_ckpt + (size_t)(n / Lo.K) * Lo.F, phi,
                                             NB, cudaMemcpyDeviceToDevice, st);
             if (e) return cuda_fail(e, "store checkpoint");
         }
-        s = step_any(g, o, phi, target, dt, ws, st);
+        if (Lo.keep_all && rk > 1) {  // the stage inputs written where the reverse reads them
+            char* w1 = (char*)ws + Lo.off_segw + (size_t)n * (rk - 1) * Lo.F;
+            char* w2 = rk == 3 ? w1 + Lo.F : nullptr;
+            s = o->dtype == LSP_F64
+                    ? enqueue_step<double>(g, o, (double*)phi, (const double*)target, dt, ws, st,
+                                           (double*)w1, (double*)w2)
+                    : enqueue_step<float>(g, o, (float*)phi, (const float*)target, dt, ws, st,
+                                          (float*)w1, (float*)w2);
+        } else {
+            s = step_any(g, o, phi, target, dt, ws, st);
+        }
     }
     if (s) return s;
     if (o->check_finite) return read_flags(ws, st);

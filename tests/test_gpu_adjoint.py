@@ -94,13 +94,14 @@ def test_fp32_adjoint_matches_oracle(kind, scheme, rk):
 
 def test_checkpoint_counts_agree():
     """sqrt(N) checkpointing recomputes the same states: any checkpoint
-    count gives the same gradient (up to the order of the FP64 parameter
-    sums and of the boundary folds)."""
+    count, and keeping every state and stage input (ncheck < 0), gives the
+    same gradient (up to the order of the FP64 parameter sums and of the
+    boundary folds)."""
     spec, phi0, g, _ = _case("air3d", "weno5", "f64")
     nsteps = 9
     lamT = np.random.default_rng(5).standard_normal(spec["n"])
     ref = _gpu_adjoint(spec, phi0, g, nsteps, lamT, ncheck=0)
-    for nc in (1, 2, 9):
+    for nc in (1, 2, 9, -1):
         got = _gpu_adjoint(spec, phi0, g, nsteps, lamT, ncheck=nc)
         assert np.abs(got[1] - ref[1]).max() <= 1e-12 * np.abs(ref[1]).max()
         np.testing.assert_allclose(got[3], ref[3], rtol=1e-12, atol=1e-14)

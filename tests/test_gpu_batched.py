@@ -36,7 +36,7 @@ def test_batched_equals_single_problem_solves(use_graph):
     for i, sp in enumerate(specs):
         P = B.Problem(sp)
         if sp["ndim"] == 3:
-            P.set_tile(16, 16, 32, 3, 2)  # the paired body the batched kernel runs for WENO5
+            P.set_tile(16, 16, 64, 3, 2)  # the paired body the batched kernel runs for WENO5
         y = to_dev(phis[i], "f32")
         st = P.solve(y, gts[i])
         torch.cuda.synchronize()
@@ -185,7 +185,7 @@ def test_batched_tile_shapes(tiles):
         P = B.Problem(sp)
         if sp["ndim"] == 3:
             tb, ta = shapes[(tiles >> 2) & 3]
-            P.set_tile(tb, ta, 32, 3, 2)
+            P.set_tile(tb, ta, 64, 3, 2)
         y = to_dev(phis[i], "f32")
         st = P.solve(y, gts[i])
         torch.cuda.synchronize()

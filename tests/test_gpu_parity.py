@@ -307,6 +307,45 @@ def test_face_shared_runs_parity(kind, scheme):
         assert np.all(got <= g)
 
 
+@pytest.mark.parametrize("scheme", ["eno3", "weno5", "upwind1"])
+@pytest.mark.parametrize("kind", ["car4d", "periodic4d", "extrap4d"])
+def test_scalar_4d_body_on_ragged_grids(kind, scheme):
+    """The scalar tiled body on 4-D grids (the slowest axis' window loaded
+    per node, periodic ends wrapped, extrapolated ends substituted): rates
+    and whole RK3 steps against the oracle on ragged grids, for tiles with
+    partial rows, one-plane chunks and chunks longer than the axis."""
+    if kind == "car4d":
+        spec = W.car4d(n=9, scheme=scheme)[0]
+        spec["n"] = [11, 13, 17, 23]
+    elif kind == "periodic4d":
+        spec = W.problem(4, [9, 10, 13, 33], [-1, -1, 0, -2], [1, 1.5, 2 * np.pi, 1],
+                         [True, True, True, True], scheme, "normal_speed", [1.3], rk=3, cfl=0.75)
+    else:
+        spec = W.problem(4, [8, 12, 11, 30], [-1, -1, 0, -2], [1, 1.5, 2 * np.pi, 1],
+                         [False, False, False, False], scheme, "translate", [0.7, -1.1, 0.4, 0.9],
+                         rk=3, cfl=0.75)
+    spec["tube"] = True
+    phi = rounded(W.smooth_field(spec, seed=8) + 0.2 * W.rough_field(spec, seed=9), "f32")
+    g = rounded(phi + 0.05 * W.smooth_field(spec, seed=3), "f32")
+    want, alpha = oracle.rate(spec, phi)
+    a = oracle.alpha(spec, phi)
+    dt = oracle.cfl_dt(spec, a, 0.75, 0.0, 10.0)
+    want_step = oracle.step(spec, phi, dt, 3, target=g)
+    tol_step = 3 * dt * rate_tol(spec, phi, want, alpha) + 8 * U32 * np.abs(phi).max()
+    allow = step_flip_allowance(spec, phi, dt, 3, alpha, tol_step)
+    for tile in [(16, 8, 5, 2, 0), (14, 17, 13, 3, 0), (32, 8, 1, 4, 0), (16, 16, 200, 3, 0)]:
+        P = B.Problem(spec, check_finite=True)
+        P.set_tile(*tile)
+        assert P.tile() == tile
+        x = to_dev(phi, "f32")
+        out = torch.empty_like(x)
+        P.rate(x, out)
+        compare(out.double().cpu().numpy(), want, rate_tol(spec, phi, want, alpha),
+                flip_allowance(spec, phi, alpha), max_frac=0.05)
+        P.step(x, to_dev(g, "f32"), t=0.0, dt=dt)
+        compare(x.double().cpu().numpy(), want_step, tol_step, allow)
+
+
 def test_face_shared_runs_reject_other_schemes_and_widths():
     """pair = 3 exists for ENO2/ENO3 with runs of 16, 28 or 32 nodes per
     CTA: other widths are refused by lsp_set_tile, and a WENO5 grid given a
