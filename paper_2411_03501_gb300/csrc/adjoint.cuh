@@ -383,6 +383,25 @@ __host__ __device__ constexpr int adj_gather_slots(int ndim) { return 7 * ndim +
 template <int NDIM, typename R>
 __host__ __device__ constexpr size_t adj_a_smem_bytes() { return sizeof(R) == 4 ? 2 * adj_gather_slots(NDIM) * 256 * sizeof(float) : 0; }
 
+// Element k of a small array, k known only at run time: a select over the
+// compile-time indices (the array stays in registers).
+template <int N, typename T>
+__device__ __forceinline__ T pick(const T* arr, int k)
+{
+    T v = arr[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j)
+        if (k == j) v = arr[j];
+    return v;
+}
+template <int N, typename T>
+__device__ __forceinline__ void put(T* arr, int k, T v)
+{
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+        if (k == j) arr[j] = v;
+}
+
 // 3 CTAs of 256 per SM in FP32: the kernel fits 80 registers without spills
 // (left to itself the compiler takes 128 and runs 2 CTAs per SM; 64
 // registers spill); FP64 (the oracle comparisons) keeps 2.
@@ -492,25 +511,37 @@ __global__ void __launch_bounds__(256, adj_a_min_blocks<R>()) adj_stage_a(AdjArg
         } else {
             lam_in = a.lam[idx];
         }
-        R x[NDIM], pm[NDIM], pp[NDIM], pbar[NDIM], win[NDIM][7];
+        // The per-axis work runs in loops that are not unrolled (one copy of
+        // the window load, the derivative and the window gradient in the
+        // code instead of NDIM: the unrolled form was bound by instruction
+        // fetch); per-axis values go in and out of the small arrays by
+        // selects over compile-time indices, so they stay in registers.
+        R x[NDIM], pm[NDIM], pp[NDIM], pbar[NDIM];
         R diss = R(0);
+        // the stencil window of axis k at this node (ghost cells substituted)
+        auto window = [&](int k, R* u) {
+            const int nk = pick<NDIM>(a.n, k), ck = pick<NDIM>(c, k);
+            const int sk = pick<NDIM>(a.stride, k);
+            if (ck >= 3 && ck < nk - 3) {  // no ghost cells in the window
+                const R* p0 = a.u + idx;
 #pragma unroll
+                for (int o = -3; o <= 3; ++o) u[o + 3] = __ldg(p0 + (long long)o * sk);
+            } else {
+                load_window<R, 3>(a.u, idx, ck, nk, sk, pick<NDIM>(a.periodic, k), u);
+            }
+        };
+#pragma unroll 1
         for (int k = 0; k < NDIM; ++k) {
             R u[7];
-            if (c[k] >= 3 && c[k] < a.n[k] - 3) {  // no ghost cells in the window
-                const R* p0 = a.u + idx;
-                const long long s = a.stride[k];
-#pragma unroll
-                for (int o = -3; o <= 3; ++o) u[o + 3] = __ldg(p0 + o * s);
-            } else {
-                load_window<R, 3>(a.u, idx, c[k], a.n[k], a.stride[k], a.periodic[k], u);
-            }
-#pragma unroll
-            for (int o = 0; o < 7; ++o) win[k][o] = u[o];
-            deriv_fast<SCHEME>(u + (3 - G), a.inv_dx[k], weno_floor12(a.inv_dx[k]), pm[k], pp[k]);
-            pbar[k] = R(0.5) * (pp[k] + pm[k]);
-            diss += a.alpha[k] * R(0.5) * (pp[k] - pm[k]);
-            x[k] = a.lo[k] + R(c[k]) * a.h[k];
+            window(k, u);
+            const R idk = pick<NDIM>(a.inv_dx, k);
+            R pmk, ppk;
+            deriv_fast<SCHEME>(u + (3 - G), idk, weno_floor12(idk), pmk, ppk);
+            put<NDIM>(pm, k, pmk);
+            put<NDIM>(pp, k, ppk);
+            put<NDIM>(pbar, k, R(0.5) * (ppk + pmk));
+            diss += pick<NDIM>(a.alpha, k) * R(0.5) * (ppk - pmk);
+            put<NDIM>(x, k, pick<NDIM>(a.lo, k) + R(pick<NDIM>(c, k)) * pick<NDIM>(a.h, k));
         }
         R sth = R(0), cth = R(1);
         if constexpr (DYN == AIR3D || DYN == CAR4D) rsincos(x[2], &sth, &cth);
@@ -533,16 +564,21 @@ __global__ void __launch_bounds__(256, adj_a_min_blocks<R>()) adj_stage_a(AdjArg
         ham_grad<DYN, NDIM>(x, pbar, a.prm, sth, cth, hp, hprm);
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc_h[j] += w * -hprm[j];
-#pragma unroll
+#pragma unroll 1
         for (int k = 0; k < NDIM; ++k) {
-            acc_a[k] += w * R(0.5) * (pp[k] - pm[k]);
-            R gm[7], gp[7];
-            window_grad<SCHEME>(win[k], a.inv_dx[k], weno_floor12(a.inv_dx[k]), gm, gp);
-            const R sp = w * (R(-0.5) * hp[k] + R(0.5) * a.alpha[k]);
-            const R sm = w * (R(-0.5) * hp[k] - R(0.5) * a.alpha[k]);
+            put<NDIM>(acc_a, k,
+                      pick<NDIM>(acc_a, k) + w * R(0.5) * (pick<NDIM>(pp, k) - pick<NDIM>(pm, k)));
+            R u[7], gm[7], gp[7];
+            window(k, u);  // again: cheaper than holding NDIM windows in registers
+            const R idk = pick<NDIM>(a.inv_dx, k), alk = pick<NDIM>(a.alpha, k);
+            window_grad<SCHEME>(u, idk, weno_floor12(idk), gm, gp);
+            const R hpk = pick<NDIM>(hp, k);
+            const R sp = w * (R(-0.5) * hpk + R(0.5) * alk);
+            const R sm = w * (R(-0.5) * hpk - R(0.5) * alk);
             R* out = a.contrib + (long long)(7 * k + 3) * a.cstride + idx;  // offset 0
-            const int n = a.n[k], s = a.stride[k];
-            if (a.periodic[k] || (c[k] >= 3 && c[k] < n - 3)) {  // no ghost position to fold
+            const int n = pick<NDIM>(a.n, k), s = pick<NDIM>(a.stride, k), ck = pick<NDIM>(c, k);
+            const int perk = pick<NDIM>(a.periodic, k);
+            if (perk || (ck >= 3 && ck < n - 3)) {  // no ghost position to fold
 #pragma unroll
                 for (int o = -3; o <= 3; ++o)
                     out[(long long)o * a.cstride] = sp * gp[o + 3] + sm * gm[o + 3];
@@ -551,11 +587,11 @@ __global__ void __launch_bounds__(256, adj_a_min_blocks<R>()) adj_stage_a(AdjArg
 #pragma unroll
             for (int o = -3; o <= 3; ++o) {
                 R cf = sp * gp[o + 3] + sm * gm[o + 3];
-                const int j = c[k] + o;
-                if (!a.periodic[k] && (j < 0 || j >= n)) {
+                const int j = ck + o;
+                if (j < 0 || j >= n) {
                     // ghost of an extrapolated axis: u_j = (1+q) u_b - q u_b', fold now
                     if (cf != R(0)) {
-                        const long long line0 = (long long)idx - (long long)c[k] * s;
+                        const long long line0 = (long long)idx - (long long)ck * s;
                         if (j < 0) {
                             const R q = R(-j);
                             atomicAdd(a.lam_u + line0, (R(1) + q) * cf);
