@@ -74,7 +74,12 @@ class _LossFn(torch.autograd.Function):
 
 
 class HJTube:
-    """A fixed-step reachable-tube solve with a discrete-adjoint backward."""
+    """A fixed-step reachable-tube solve with a discrete-adjoint backward.
+
+    ncheck: checkpoints of the forward (0: ceil(sqrt(nsteps)), recomputed
+    segment by segment in the backward); negative: every state and stage
+    input is kept (nsteps * rk fields of workspace) and the backward
+    recomputes nothing."""
 
     def __init__(self, spec: dict, nsteps: int, ncheck: int = 0, device="cuda"):
         self.spec = spec
