@@ -8,8 +8,10 @@ One benchmark step = one complete reachable-tube solve of the workload
 metric is  points * stages / time.  Default workload: the 4-D car at 81^4
 (ENO3, RK3, CFL 0.75, t_final 1.0, FP32; 124 steps, 372 stages; 43 M nodes,
 fields of 172 MB), the largest configuration that fits one GPU; the air3d
-game at 201^3 (WENO5, RK3, t_final 2.8; 5241 stages) is measured first and
-reported inside the same line under "also".
+game at 201^3 (WENO5, RK3, t_final 2.8; 5241 stages), the batched workload
+(256 problems in one persistent launch) and the differentiation workload
+(air3d 129^3, 200 RK3 steps, gradient by the discrete adjoint) are measured
+first and reported inside the same line under "also".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...   # the FP64 oracle on the host cores
@@ -424,22 +426,30 @@ def measure_solve(args, name: str, rank: int, world: int, local_rank: int, clk_t
 
     # ---- roofline of the dominant kernel (the fused stage kernel): its
     # average launch time over the timed region = solve time / stage launches
-    per_launch_s = (ms / 1e3) / (stages * args.steps)
     bpn, fpn = algorithmic(spec)
-    roof = roofline_of(fpn * npts, bpn * npts, per_launch_s, measured_traffic(spec["name"]))
+    fused = tile[0] > 0 and tile[4] == 5 and spec["rk"] == 2
+    launches = stats["steps"] if fused else stages
+    per_launch_s = (ms / 1e3) / (launches * args.steps)
+    if fused:  # both RK2 stages per launch: phi (and the target) in, phi' out
+        word = 8 if spec["dtype"] == "f64" else 4
+        roof = roofline_of(2 * fpn * npts, word * (2 + bool(spec.get("tube"))) * npts,
+                           per_launch_s, None)
+    else:
+        roof = roofline_of(fpn * npts, bpn * npts, per_launch_s, measured_traffic(spec["name"]))
     return {
         "spec": spec, "phi0": phi0, "g": g, "value": value, "ms_per_step": ms / args.steps,
         "config": {"workload": spec["name"], "points": npts, "stages_per_step": stages,
                    "rk_steps_per_step": stats["steps"],
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed (512 MB write) between timed solves",
-                   "graph": bool(args.graph), "tile": list(tile)},
+                   "graph": bool(args.graph), "tile": list(tile),
+                   "fused_rk2_steps": fused},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo,
                 "pipelined": "step i+1's uploads and step i-1's download overlap step i's solve "
                              "(second stream, two buffer sets)",
                 "copy_ms_per_step_alone": copy_ms},
-        "gpu_launches": stages * args.steps,
+        "gpu_launches": launches * args.steps,
         "roofline": roof,
         "clocks": clk.summary(),
     }
@@ -508,6 +518,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
                 "e2e": r["e2e"]["value"], "roofline": r["roofline"], "tile": r["config"]["tile"],
                 "stages_per_step": r["config"]["stages_per_step"], "clocks": r["clocks"]}
+    extras = [] if args.extras in ("", "none") else args.extras.split(",")
+    for name in extras:  # the batched and differentiation workloads, same process
+        fn = {"batched": run_batched, "adjoint": run_adjoint}[name]
+        ln = fn(args, rank, world, local_rank, emit=False)
+        if isinstance(ln, dict):
+            others[ln["config"]["workload"]] = {
+                k: ln[k] for k in ("value", "unit", "ms_per_step", "e2e", "roofline", "config",
+                                   "gpu_launches", "clocks", "scaling")}
     r = measure_solve(args, args.workload, rank, world, local_rank, "main")
     if rank != 0:
         return 0
@@ -526,7 +544,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     return 0
 
 
-def run_batched(args, rank: int, world: int, local_rank: int):
+def run_batched(args, rank: int, world: int, local_rank: int, emit: bool = True):
     """The batched workload: 256 problems (half 2-D normal speed, half 3-D
     air3d, seeded sizes/speeds/radii) in one batched solve per benchmark
     step; ranks split the problems by estimated cost (sharding.shard, no
@@ -692,11 +710,13 @@ def run_batched(args, rank: int, world: int, local_rank: int):
         "gpu_launches": launches * args.steps,
         "roofline": roof, "cpu_baseline": None, "clocks": clk.summary(),
     }
+    if not emit:
+        return line
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_adjoint(args, rank: int, world: int, local_rank: int):
+def run_adjoint(args, rank: int, world: int, local_rank: int, emit: bool = True):
     """The differentiation workload: the air3d tube at 129^3 in FP32 over 200
     fixed RK3 steps; loss = smoothed volume of {phi <= 0} + phi at 1024 seeded
     query states.  One benchmark step = forward solve keeping every state and
@@ -830,6 +850,8 @@ def run_adjoint(args, rank: int, world: int, local_rank: int):
         "gpu_launches": adjoint_launches(nsteps, 3, tube.ncheck) * args.steps, "roofline": None,
         "cpu_baseline": None, "clocks": clk.summary(),
     }
+    if not emit:
+        return line
     print(json.dumps(line), flush=True)
     return 0
 
@@ -974,6 +996,10 @@ def main():
     ap.add_argument("--also", default="auto",
                     help="comma-separated solve workloads measured before the main one and "
                          "reported inside its line (auto: air3d_201 with the default workload)")
+    ap.add_argument("--extras", default="auto",
+                    help="comma-separated workloads among batched, adjoint measured before the "
+                         "main one and reported under 'also' (auto: both with the default "
+                         "workload)")
     ap.add_argument("--graph", type=int, default=0)
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--outdir", default=os.path.join(ROOT, "bench_out"),
@@ -1008,6 +1034,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.also == "auto":
         args.also = "air3d_201" if args.workload == "car4d_81" and args.mode == "solve" else ""
+    if args.extras == "auto":
+        args.extras = ("batched,adjoint" if args.workload == "car4d_81" and args.mode == "solve"
+                       else "")
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if world > 1:

@@ -242,7 +242,19 @@ lsp_status lsp_hj_solve(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
  * pair = 4 is the same with runs of 2 nodes (tb/2 x ta threads, minb 3: 80
  * registers, more resident warps).
  * Its results agree with the other variants to FP32 rounding, not bit for
- * bit (the same selections, the arithmetic grouped differently).  A tile
+ * bit (the same selections, the arithmetic grouped differently).
+ * pair = 5 (3-D grids, any scheme) is temporal blocking of TVD-RK2: both
+ * stages of a step in one launch, the first stage evaluated in shared memory
+ * on the tile plus its halo (G cells along the tile axes, G planes at each
+ * end of the chunk) and the second on the tile, with the same operations
+ * as the scalar body (pair 0), so the result equals two scalar-body stages.
+ * It serves RK2 steps and solves with GLF dissipation, no clip and dynamics
+ * with state-only bounds; lsp_hj_solve then alternates phi and the
+ * workspace's stage field (copying the result to phi at the end when the
+ * step count is odd), lsp_hj_step writes the stage field and copies it
+ * back.  Every other stage on such a tile (RK1, RK3, lsp_hj_rate, the
+ * adjoint's forward) runs the scalar body of the same tile.  lsp_autotune
+ * does not try it.  A tile
  * whose pair the scheme
  * has no variant for makes the step use the generic kernel.  With local
  * dissipation coefficients or the variational clip (opts->diss, varform),
@@ -259,7 +271,10 @@ lsp_status lsp_hj_solve(lsp_grid* grid, const lsp_solve_opts* opts, void* phi,
  *        pair is 0, 1 or 2 with tb*ta <= 256 and the haloed tile fitting 3
  *        values per thread, or pair is 3 (4) with tb in {16, 28, 32},
  *        (tb/4)*ta <= 256 ((tb/2)*ta <= 256) and two staged planes within
- *        200 KB of shared memory.
+ *        200 KB of shared memory, or pair is 5 on a 3-D grid with tb*ta <=
+ *        256, the tile with a 4-cell halo fitting 4 values per thread and
+ *        with a 2-cell halo 3 (checked for ENO2; a step whose scheme's
+ *        halo does not fit runs the generic kernel).
  * lsp_get_tile reports the tile a step with `opts` would use (all -1 when
  * the generic kernel runs). */
 lsp_status lsp_set_tile(lsp_grid* grid, int tb, int ta, int ch, int minb, int pair);

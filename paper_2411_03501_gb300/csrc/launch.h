@@ -36,6 +36,12 @@ template <int R>
 cudaError_t launch_stage_run_r(int ndim, int scheme, int dyn, const StageArgs<float>& a,
                                const Tile& t, cudaStream_t s);
 bool run_tile_ok(int ndim, int scheme, int run, int tb, int ta);
+// The two stages of a TVD-RK2 step in one launch (stage_fused.cuh, Tile.pair
+// = 5): 3-D FP32 grids, GLF with state-only bounds; a.phi_s = phi^n, a.out =
+// phi^{n+1} (a different field), a.dt the step.
+cudaError_t launch_stage_fused_rk2(int scheme, int dyn, const StageArgs<float>& a, const Tile& t,
+                                   cudaStream_t s);
+bool fused_tile_ok(int ndim, int scheme, const Tile& t, const int* n);
 // The same stage with local coefficients / the variational clip compiled in
 // (stage_tiled_local.cu); launch_stage_tiled routes there when a asks for them.
 cudaError_t launch_stage_tiled_local(int ndim, int scheme, int dyn, const StageArgs<float>& a,

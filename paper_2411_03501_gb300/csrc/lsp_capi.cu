@@ -261,9 +261,49 @@ lsp_status enqueue_step(const lsp_grid* g, const lsp_solve_opts* o, R* phi, cons
     }
 }
 
-lsp_status step_any(const lsp_grid* g, const lsp_solve_opts* o, void* phi, const void* target,
-                    double dt, void* ws, cudaStream_t st)
+// Does an RK2 step with these options run as one temporally blocked launch
+// (tile pair 5; 3-D FP32, GLF with state-only bounds)?
+bool fused_rk2(const lsp_grid* g, const lsp_solve_opts* o)
 {
+    if (o->rk_order != 2 || o->dtype != LSP_F32 || g->ndim != 3 || !g->alpha_state) return false;
+    if (o->diss != LSP_DISS_GLF || o->varform) return false;
+    const lsp::Tile t = tile_in_effect(g, o);
+    return t.ch > 0 && t.pair == 5;
+}
+
+// One RK2 step from phi into out (distinct fields) in one launch.
+lsp_status enqueue_fused_rk2(const lsp_grid* g, const lsp_solve_opts* o, const float* phi,
+                             float* out, const float* target, double dt, void* ws, cudaStream_t st)
+{
+    lsp::StageArgs<float> a = base_args<float>(g, (lsp::Ctl*)ws);
+    a.phi_s = phi;
+    a.out = out;
+    a.target = target;
+    a.dt = float(dt);
+    a.c_n = 0.5f;
+    a.c_s = 0.5f;
+    a.c_l = 0.5f;
+    a.tube = o->tube ? 1 : 0;
+    cudaError_t e = lsp::launch_stage_fused_rk2(o->scheme, g->dyn, a, tile_in_effect(g, o), st);
+    if (e != cudaSuccess) return cuda_fail(e, "fused RK2 kernel");
+    return LSP_OK;
+}
+
+// One step of phi in place.  allow_fused: a fused-RK2 tile runs the step
+// as one launch into the workspace's stage field, copied back to phi (the
+// solve alternates the two fields instead of copying).
+lsp_status step_any(const lsp_grid* g, const lsp_solve_opts* o, void* phi, const void* target,
+                    double dt, void* ws, cudaStream_t st, bool allow_fused = false)
+{
+    if (allow_fused && fused_rk2(g, o)) {
+        float* w1 = (float*)((char*)ws + lsp::kCtlBytes);
+        lsp_status s = enqueue_fused_rk2(g, o, (const float*)phi, w1, (const float*)target, dt, ws, st);
+        if (s) return s;
+        if (cudaError_t e = cudaMemcpyAsync(phi, w1, (size_t)g->npts * sizeof(float),
+                                            cudaMemcpyDeviceToDevice, st))
+            return cuda_fail(e, "copy back");
+        return LSP_OK;
+    }
     if (o->dtype == LSP_F64)
         return enqueue_step<double>(g, o, (double*)phi, (const double*)target, dt, ws, st);
     return enqueue_step<float>(g, o, (float*)phi, (const float*)target, dt, ws, st);
@@ -544,7 +584,7 @@ lsp_status lsp_hj_step(lsp_grid* g, const lsp_solve_opts* o, void* phi, const vo
     }
     if (!std::isfinite(dt) || !(dt > 0.0)) return fail(LSP_EINVAL, "step size must be finite and > 0");
     *dt_io = dt;
-    if ((s = step_any(g, o, phi, target, dt, ws, st))) return s;
+    if ((s = step_any(g, o, phi, target, dt, ws, st, true))) return s;
     if (o->check_finite) return read_flags(ws, st);
     return LSP_OK;
 }
@@ -612,17 +652,32 @@ lsp_status lsp_hj_solve(lsp_grid* g, const lsp_solve_opts* o, void* phi, const v
     }
     s = reset_flags(ws, es);
     double t = t0;
+    // fused RK2: each step reads one field and writes the other (phi and the
+    // workspace's stage field in turn), the result copied to phi at the end
+    const bool fused = fused_rk2(g, o);
+    float* cur = (float*)phi;
+    float* alt = (float*)((char*)ws + lsp::kCtlBytes);
     while (!s && t < t_stop) {
         const double dt = cfl_dt_host(g, o->cfl, t, t_final);
         if (!(dt > 0.0)) {
             s = fail(LSP_EINVAL, "non-positive CFL step");
             break;
         }
-        s = step_any(g, o, phi, target, dt, ws, es);
+        if (fused) {
+            s = enqueue_fused_rk2(g, o, cur, alt, (const float*)target, dt, ws, es);
+            std::swap(cur, alt);
+        } else {
+            s = step_any(g, o, phi, target, dt, ws, es);
+        }
         t += dt;
         sts.steps++;
         sts.dt_min = std::fmin(sts.dt_min, dt);
         sts.dt_max = std::fmax(sts.dt_max, dt);
+    }
+    if (!s && fused && cur != (float*)phi) {
+        if (cudaError_t e = cudaMemcpyAsync(phi, cur, (size_t)g->npts * sizeof(float),
+                                            cudaMemcpyDeviceToDevice, es))
+            s = cuda_fail(e, "copy back");
     }
     sts.t_end = t;
     sts.stages = sts.steps * o->rk_order;
@@ -669,7 +724,8 @@ lsp_status lsp_set_tile(lsp_grid* g, int tb, int ta, int ch, int minb, int pair)
     lsp::Tile t{tb, ta, ch, minb, pair};
     // validated for a scheme that has the variant (the step re-checks the
     // tile against its own scheme and runs the generic kernel if it fails)
-    if (!lsp::tile_valid(g->ndim, pair >= 3 ? LSP_ENO3 : LSP_WENO5, t, g->n))
+    if (!lsp::tile_valid(g->ndim, pair == 5 ? LSP_ENO2 : (pair >= 3 ? LSP_ENO3 : LSP_WENO5), t,
+                         g->n))
         return fail(LSP_EINVAL, "tile %dx%dx%d (%d CTAs/SM) is not valid for this grid", tb, ta,
                     ch, minb);
     g->tile = t;

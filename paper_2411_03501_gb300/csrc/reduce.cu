@@ -33,6 +33,7 @@ bool tile_valid(int ndim, int scheme, const Tile& t, const int* n)
     if (t.minb < 2 || t.minb > 4) return false;
     const int nS = n[ndim - 3];
     const long long nz = (long long)((nS + t.ch - 1) / t.ch) * (ndim == 4 ? n[0] : 1);
+    if (t.pair == 5) return fused_tile_ok(ndim, scheme, t, n);  // temporally blocked RK2
     if (t.pair == 3 || t.pair == 4) {  // face-shared ENO runs of 4 or 2 nodes
         return (scheme == ENO2 || scheme == ENO3) &&
                run_tile_ok(ndim, scheme, t.pair == 3 ? 4 : 2, t.tb, t.ta) && nz <= 65535;
@@ -68,6 +69,10 @@ cudaError_t launch_stage_tiled(int ndim, int scheme, int dyn, const StageArgs<fl
         // tile of the same chunking runs the local body
         const Tile tl = t.pair >= 3 ? Tile{32, 8, t.ch, 3, 0} : t;
         return launch_stage_tiled_local(ndim, scheme, dyn, a, tl, s);
+    }
+    if (t.pair == 5) {  // a single stage on a fused-RK2 tile: the scalar body
+        const Tile ts{t.tb, t.ta, t.ch, t.minb, 0};
+        return launch_stage_tiled(ndim, scheme, dyn, a, ts, s);
     }
     if (t.pair == 3) return launch_stage_run_r<4>(ndim, scheme, dyn, a, t, s);
     if (t.pair == 4) return launch_stage_run_r<2>(ndim, scheme, dyn, a, t, s);
