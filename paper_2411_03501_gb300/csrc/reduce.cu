@@ -67,7 +67,8 @@ cudaError_t launch_stage_tiled(int ndim, int scheme, int dyn, const StageArgs<fl
     if ((a.local_alpha || a.varform) && !(scheme == WENO5 && t.pair == 2 && dyn != QUADRATIC)) {
         // the face-shared runs have no local variant: a one-node-per-thread
         // tile of the same chunking runs the local body
-        const Tile tl = t.pair >= 3 ? Tile{32, 8, t.ch, 3, 0} : t;
+        const Tile tl = (t.pair == 3 || t.pair == 4) ? Tile{32, 8, t.ch, 3, 0}
+                                                     : Tile{t.tb, t.ta, t.ch, t.minb, 0};
         return launch_stage_tiled_local(ndim, scheme, dyn, a, tl, s);
     }
     if (t.pair == 5) {  // a single stage on a fused-RK2 tile: the scalar body
