@@ -17,6 +17,16 @@ oracle adjoint instead.
   python tests/precision_report.py air3d_201 car4d_81 batched adjoint
   python tests/precision_report.py --gpu-only DIR air3d_201 batched adjoint
   python tests/precision_report.py --oracle-only DIR air3d_201 batched adjoint
+  python tests/precision_report.py --oracle-only DIR --conditioning air3d_121 car4d_51
+
+With --conditioning the oracle side also computes, for the single-problem
+configurations, its own per-node response R to FP32-sized noise injected into
+every step (two realisations, tests/conditioning.py) and the ill-conditioned
+set C (R above a third of the bar, grown by one node), and reports
+  frac_C                the fraction of nodes in C
+  frac_over_bar_off_C   nodes above the bar outside C (the kernel's share)
+  err_off_C             max|dphi| / max|phi| outside C
+  worst_in_C_over_3R    max over C of |dphi| / (3 R)
 
 The two-phase form runs the GPU side on a GPU host and writes its results
 (FP32 fields, gradients, step counts, tiles) to DIR/<config>.npz; the oracle
@@ -35,7 +45,7 @@ sys.path.insert(0, HERE)
 sys.path.insert(0, os.path.dirname(HERE))
 
 import oracle  # noqa: E402
-from conditioning import BAR, boundary_distance  # noqa: E402
+from conditioning import BAR, boundary_distance, conditioning_mask, noise_response  # noqa: E402
 from gpu_helpers import rounded, sign_ok  # noqa: E402
 
 
@@ -105,7 +115,7 @@ def gpu_phase(name, out):
     return {"phi": got, "steps": np.array(steps), "tile": np.array(tile)}
 
 
-def oracle_phase(name, d):
+def oracle_phase(name, d, conditioning=False):
     """Compare one configuration's GPU arrays `d` with the oracle."""
     if name == "batched":
         from paper_2411_03501_gb300 import workloads as W
@@ -125,8 +135,24 @@ def oracle_phase(name, d):
     spec, phi0, g = _inputs(name)
     t0 = time.time()
     want, so = oracle.solve(spec, phi0, spec["t_final"], spec["rk"], spec["cfl"], target=g)
-    return [_report(name, spec, d["phi"].astype(np.float64), want, int(d["steps"]), so["steps"],
-                    d["tile"], time.time() - t0)]
+    got = d["phi"].astype(np.float64)
+    rep = _report(name, spec, got, want, int(d["steps"]), so["steps"], d["tile"],
+                  time.time() - t0)
+    if conditioning:
+        t1 = time.time()
+        R = noise_response(oracle, spec, phi0, g, spec["t_final"], want)
+        scale = float(np.abs(want).max())
+        C, Rd = conditioning_mask(R, scale, spec)
+        err = np.abs(got - want)
+        off = ~C
+        rep.update({"frac_C": float(C.mean()),
+                    "frac_over_bar_off_C": float(((err > BAR * scale) & off).mean()),
+                    "err_off_C": float(err[off].max()) / scale if off.any() else None,
+                    "worst_in_C_over_3R": (float((err[C] / (3.0 * Rd[C])).max())
+                                           if C.any() else None),
+                    "noise_response_max": float(R.max()) / scale,
+                    "conditioning_s": time.time() - t1})
+    return [rep]
 
 
 ADJ_N, ADJ_STEPS = 129, 200
@@ -197,6 +223,8 @@ def main(argv):
     if argv and argv[0] in ("--gpu-only", "--oracle-only"):
         mode, outdir, argv = argv[0][2:], argv[1], argv[2:]
         os.makedirs(outdir, exist_ok=True)
+    conditioning = "--conditioning" in argv
+    argv = [a for a in argv if a != "--conditioning"]
     names = argv or ["air3d_201", "car4d_81", "batched", "adjoint"]
     for name in names:
         path = os.path.join(outdir, f"{name}.npz") if outdir else None
@@ -208,7 +236,7 @@ def main(argv):
         if mode == "oracle-only":
             d = dict(np.load(path))
         if mode in ("both", "oracle-only"):
-            for r in oracle_phase(name, d):
+            for r in oracle_phase(name, d, conditioning):
                 print(json.dumps(r), flush=True)
 
 

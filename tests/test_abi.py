@@ -98,3 +98,29 @@ def test_product_path_fails_loudly_without_library(tmp_path):
             B.load(str(tmp_path / "missing.so"))
     finally:
         B._lib = saved
+
+
+def test_fused_rk2_tile_validation_on_host(lib):
+    """Tile variant 5 (both RK2 stages in one launch): accepted on 3-D grids
+    when the tile with a 4-node halo fits 4 staged values per thread and with
+    a 2-node halo 3 (ENO2's halo); a scheme with a wider halo that does not
+    fit runs the generic kernel (reported as all -1); refused on 4-D grids
+    and for tiles of more than 256 threads."""
+    from paper_2411_03501_gb300 import binding as B
+    g = B.lsp_grid_create(3, [0] * 3, [1] * 3, [37, 29, 45], ["extrapolate"] * 3)
+    B.lsp_set_dynamics(g, "quadratic", [])  # no device work
+    eno2 = B.make_opts(rk_order=2, scheme="eno2", dtype="f32")
+    eno3 = B.make_opts(rk_order=2, scheme="eno3", dtype="f32")
+    B.lsp_set_tile(g, 32, 8, 5, 3, 5)
+    assert B.lsp_get_tile(g, eno2) == (32, 8, 5, 3, 5)
+    assert B.lsp_get_tile(g, eno3) == (32, 8, 5, 3, 5)  # (14 x 38, 20 x 44 fit)
+    B.lsp_set_tile(g, 64, 4, 5, 3, 5)
+    assert B.lsp_get_tile(g, eno2) == (64, 4, 5, 3, 5)
+    assert B.lsp_get_tile(g, eno3) == (-1, -1, -1, -1, -1)  # 16 x 76 > 4 x 256
+    for bad in [(8, 4, 5, 3, 5), (32, 16, 5, 3, 5), (32, 8, 5, 5, 5), (32, 8, 0, 3, 5)]:
+        with pytest.raises(B.LspError):
+            B.lsp_set_tile(g, *bad)
+    g4 = B.lsp_grid_create(4, [0] * 4, [1] * 4, [9, 8, 10, 11], ["extrapolate"] * 4)
+    B.lsp_set_dynamics(g4, "quadratic", [])
+    with pytest.raises(B.LspError):
+        B.lsp_set_tile(g4, 16, 8, 5, 3, 5)
