@@ -75,7 +75,8 @@ typedef enum { LSP_UPWIND1 = 0, LSP_ENO2 = 1, LSP_ENO3 = 2, LSP_WENO5 = 3 } lsp_
  *                        pursuer u_p in [-up, up] minimises    {a, g, ue, up}
  *  DOUBLE_INTEGRATOR d = 2  x1dot = x2, x2dot = u, |u| <= umax,
  *                        u minimises p.f (reach)                {umax}
- * The adjoint covers NORMAL_SPEED, TRANSLATE, AIR3D and CAR4D.
+ * The adjoint covers every dynamics but QUADRATIC (whose LF bound depends
+ * on the costate).
  */
 typedef enum {
     LSP_DYN_NORMAL_SPEED = 0,

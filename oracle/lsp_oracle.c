@@ -963,6 +963,27 @@ static void ham_grads(const orc_problem* P, const double* x, const double* p, do
         hprm[1] = fabs(p[3]);
         break;
     }
+    case ORC_DYN_ROCKETS: {
+        /* H = -[p1 a cos th + p2 (a sin th + a - g) + ue |p1 x - p3|
+         *       - up |p2 x + p3|]  (the closed form derived from Eq. 31)    */
+        double a = c[0], g = c[1], ue = c[2], up = c[3];
+        double X = x[0], th = x[2];
+        double s1 = p[0] * X - p[2], s2 = p[1] * X + p[2];
+        double g1 = sgn1(s1), g2 = sgn1(s2);
+        hp[0] = -(a * cos(th) + ue * g1 * X);
+        hp[1] = -(a * sin(th) + a - g - up * g2 * X);
+        hp[2] = ue * g1 + up * g2;
+        hprm[0] = -(p[0] * cos(th) + p[1] * (sin(th) + 1.0));
+        hprm[1] = p[1];
+        hprm[2] = -fabs(s1);
+        hprm[3] = fabs(s2);
+        break;
+    }
+    case ORC_DYN_DOUBLE_INT: /* H = -(p1 x2 - umax |p2|) */
+        hp[0] = -x[1];
+        hp[1] = c[0] * sgn1(p[1]);
+        hprm[0] = fabs(p[1]);
+        break;
     }
 }
 
@@ -1015,6 +1036,23 @@ static void alpha_grads(const orc_problem* P, double* dalpha /* [4][8] */)
         case ORC_DYN_CAR4D:
             if (k == 2) g[0] = 1.0;
             if (k == 3) g[1] = 1.0;
+            break;
+        case ORC_DYN_ROCKETS:
+            if (k == 0) { /* a |cos th| + ue |x| */
+                g[0] = fabs(cos(x[2]));
+                g[2] = fabs(x[0]);
+            } else if (k == 1) { /* |a sin th + a - g| + up |x| */
+                double w = c[0] * sin(x[2]) + c[0] - c[1];
+                g[0] = sgn1(w) * (sin(x[2]) + 1.0);
+                g[1] = -sgn1(w);
+                g[3] = fabs(x[0]);
+            } else { /* ue + up */
+                g[2] = 1.0;
+                g[3] = 1.0;
+            }
+            break;
+        case ORC_DYN_DOUBLE_INT:
+            if (k == 1) g[0] = 1.0; /* the bound umax */
             break;
         }
     }
@@ -1145,8 +1183,7 @@ int orc_adjoint(const orc_problem* P, const double* phi0, const double* g, int r
                 int64_t nsteps, const double* lamT, double* lam0, double* lam_g, double* dprm,
                 double* phiT)
 {
-    if (P->dyn == ORC_DYN_QUADRATIC || P->dyn == ORC_DYN_ROCKETS || P->dyn == ORC_DYN_DOUBLE_INT)
-        return -5; /* reverse written for the other dynamics */
+    if (P->dyn == ORC_DYN_QUADRATIC) return -5; /* reverse written for state-only bounds */
     if (P->diss != ORC_DISS_GLF || P->varform) return -6; /* reverse of the GLF form only */
     int d = P->ndim;
     int64_t N = orc_npoints(P);

@@ -284,6 +284,25 @@ __device__ __forceinline__ void ham_grad(const R* x, const R* p, const R* prm, R
         hp[3] = prm[1] * sgn1(p[3]);
         hprm[0] = rabs(p[2]);
         hprm[1] = rabs(p[3]);
+    } else if constexpr (DYN == ROCKETS) {
+        // H = -[p1 a cos th + p2 (a sin th + a - g) + ue |p1 x - p3| - up |p2 x + p3|];
+        // the switching arguments as hamiltonian_rockets forms them, so the
+        // frozen input signs are the forward's
+        const R a = prm[0], g = prm[1], ue = prm[2], up = prm[3];
+        const R s1 = rfma(p[0], x[0], -p[2]), s2 = rfma(p[1], x[0], p[2]);
+        const R g1 = sgn1(s1), g2 = sgn1(s2);
+        hp[0] = -rfma(ue * g1, x[0], a * c);
+        hp[1] = -rfma(-up * g2, x[0], rfma(a, s, a - g));
+        hp[2] = ue * g1 + up * g2;
+        hprm[0] = -rfma(p[0], c, p[1] * (s + R(1)));
+        hprm[1] = p[1];
+        hprm[2] = -rabs(s1);
+        hprm[3] = rabs(s2);
+    } else if constexpr (DYN == DOUBLE_INT) {
+        // H = -(p1 x2 - umax |p2|)
+        hp[0] = -x[1];
+        hp[1] = prm[0] * sgn1(p[1]);
+        hprm[0] = rabs(p[1]);
     } else {
 #pragma unroll
         for (int k = 0; k < NDIM; ++k) hp[k] = p[k];
@@ -544,7 +563,7 @@ __global__ void __launch_bounds__(256, adj_a_min_blocks<R>()) adj_stage_a(AdjArg
             put<NDIM>(x, k, pick<NDIM>(a.lo, k) + R(pick<NDIM>(c, k)) * pick<NDIM>(a.h, k));
         }
         R sth = R(0), cth = R(1);
-        if constexpr (DYN == AIR3D || DYN == CAR4D) rsincos(x[2], &sth, &cth);
+        if constexpr (DYN == AIR3D || DYN == CAR4D || DYN == ROCKETS) rsincos(x[2], &sth, &cth);
         const R H = hamiltonian_sc<DYN, NDIM>(x, pbar, a.prm, sth, cth);
         const R L = -(H - diss);
         R v = a.c_s * a.u[idx] + (a.c_l * a.dt) * L;

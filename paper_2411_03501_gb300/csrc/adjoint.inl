@@ -50,6 +50,12 @@ static cudaError_t adj_dyn(int dyn, const AdjArgs<LSP_REAL>& a, cudaStream_t s)
     case CAR4D:
         if constexpr (NDIM == 4) return launch_pass_a<4, SCHEME, CAR4D>(a, s);
         return cudaErrorInvalidValue;
+    case ROCKETS:
+        if constexpr (NDIM == 3) return launch_pass_a<3, SCHEME, ROCKETS>(a, s);
+        return cudaErrorInvalidValue;
+    case DOUBLE_INT:
+        if constexpr (NDIM == 2) return launch_pass_a<2, SCHEME, DOUBLE_INT>(a, s);
+        return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }

@@ -1444,8 +1444,7 @@ lsp_status adj_check(const lsp_grid* g, const lsp_solve_opts* o, int nsteps)
     lsp_status s = check_opts(g, o);
     if (s) return s;
     if (!g->alpha_state) return fail(LSP_EUNSUPPORTED, "the adjoint needs state-only LF bounds");
-    if (g->dyn == LSP_DYN_QUADRATIC || g->dyn == LSP_DYN_ROCKETS ||
-        g->dyn == LSP_DYN_DOUBLE_INTEGRATOR)
+    if (g->dyn == LSP_DYN_QUADRATIC)
         return fail(LSP_EUNSUPPORTED, "no adjoint for dynamics %d", g->dyn);
     if (o->diss != LSP_DISS_GLF || o->varform)
         return fail(LSP_EUNSUPPORTED, "the adjoint reverses the GLF form without the clip");
@@ -1546,6 +1545,23 @@ void alpha_param_grads(const lsp_grid* g, const double* x, int k, double* gk)
     case LSP_DYN_CAR4D:
         if (k == 2) gk[0] = 1.0;
         if (k == 3) gk[1] = 1.0;
+        break;
+    case LSP_DYN_ROCKETS:
+        if (k == 0) {  // a |cos th| + ue |x|
+            gk[0] = std::fabs(std::cos(x[2]));
+            gk[2] = std::fabs(x[0]);
+        } else if (k == 1) {  // |a sin th + a - g| + up |x|
+            const double w = c[0] * std::sin(x[2]) + c[0] - c[1];
+            gk[0] = sg(w) * (std::sin(x[2]) + 1.0);
+            gk[1] = -sg(w);
+            gk[3] = std::fabs(x[0]);
+        } else {  // ue + up
+            gk[2] = 1.0;
+            gk[3] = 1.0;
+        }
+        break;
+    case LSP_DYN_DOUBLE_INTEGRATOR:
+        if (k == 1) gk[0] = sg(c[0]);  // |umax|
         break;
     }
 }

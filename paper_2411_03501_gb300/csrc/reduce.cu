@@ -96,6 +96,8 @@ cudaError_t launch_alpha_argmax(int dyn, const GridGeom& g, const double* alpha,
     case TRANSLATE: alpha_argmax_kernel<TRANSLATE><<<nb, 256, 0, s>>>(g, alpha, out); break;
     case AIR3D: alpha_argmax_kernel<AIR3D><<<nb, 256, 0, s>>>(g, alpha, out); break;
     case CAR4D: alpha_argmax_kernel<CAR4D><<<nb, 256, 0, s>>>(g, alpha, out); break;
+    case ROCKETS: alpha_argmax_kernel<ROCKETS><<<nb, 256, 0, s>>>(g, alpha, out); break;
+    case DOUBLE_INT: alpha_argmax_kernel<DOUBLE_INT><<<nb, 256, 0, s>>>(g, alpha, out); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -124,3 +124,15 @@ def test_fused_rk2_tile_validation_on_host(lib):
     B.lsp_set_dynamics(g4, "quadratic", [])
     with pytest.raises(B.LspError):
         B.lsp_set_tile(g4, 16, 8, 5, 3, 5)
+
+
+def test_adjoint_refuses_costate_dependent_bounds(lib):
+    """The discrete adjoint reverses the GLF form with state-only bounds: for
+    H = |p|^2/2 (whose LF bound depends on the costate) it is refused on the
+    host, before any device work."""
+    from paper_2411_03501_gb300 import binding as B
+    g = B.lsp_grid_create(3, [0] * 3, [1] * 3, [9, 8, 10], ["extrapolate"] * 3)
+    B.lsp_set_dynamics(g, "quadratic", [])
+    with pytest.raises(B.LspError) as e:
+        B.lsp_adjoint_workspace_size(g, B.make_opts(rk_order=3, scheme="weno5"), 4, 0)
+    assert e.value.status == B.LSP_EUNSUPPORTED

@@ -23,6 +23,16 @@ def _case(kind, scheme, dtype, rk=3):
         spec = W.car4d(n=8, scheme=scheme, dtype=dtype)[0]
         spec["n"] = [9, 8, 9, 8]
         nsteps = 3
+    elif kind == "rockets":
+        spec = W.rockets(n=12, scheme=scheme, a=1.1, g=30.0, ue=0.9, up=1.2, dtype=dtype)[0]
+        spec["n"] = [13, 12, 11]
+        spec["rk"] = rk
+        nsteps = 4
+    elif kind == "double_integrator":
+        spec = W.double_integrator(n=17, scheme=scheme, umax=0.8, dtype=dtype)[0]
+        spec["n"] = [17, 15]
+        spec["rk"] = rk
+        nsteps = 5
     else:
         spec = W.problem(2, [17, 15], [-1, -1], [1, 1], [False, True], scheme, "normal_speed",
                          [1.3], rk=rk, cfl=0.75, tube=True, dtype=dtype)
@@ -50,7 +60,8 @@ def _gpu_adjoint(spec, phi0, g, nsteps, lamT, ncheck=0):
 
 
 CASES = [("air3d", "weno5", 3), ("air3d", "eno3", 3), ("air3d", "eno2", 2),
-         ("air3d", "upwind1", 1), ("car4d", "eno3", 3), ("normal2d", "weno5", 3)]
+         ("air3d", "upwind1", 1), ("car4d", "eno3", 3), ("normal2d", "weno5", 3),
+         ("rockets", "eno2", 2), ("rockets", "weno5", 3), ("double_integrator", "eno2", 2)]
 
 
 @pytest.mark.parametrize("kind,scheme,rk", CASES)

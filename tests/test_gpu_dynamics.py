@@ -1,8 +1,8 @@
 """The rockets game (Sec. VI-A, Eq. 31) and the double integrator (Table I)
 on the GPU through the C ABI against the FP64 oracle: GLF coefficients,
 rates of every scheme and kernel family (generic, tiled, paired WENO5
-variants; global and local coefficients), whole tube solves, batched solves,
-and the adjoint's refusal."""
+variants; global and local coefficients), whole tube solves and batched
+solves (their adjoint: test_gpu_adjoint.py)."""
 import numpy as np
 import pytest
 import torch
@@ -114,10 +114,3 @@ def test_batched_new_dynamics_match_single_solves():
         else:
             assert float((xs[i] - y).abs().max()) <= 1e-5 * float(y.abs().max())
 
-
-def test_adjoint_refuses_new_dynamics():
-    for spec in (W.rockets(n=9, dtype="f64")[0], W.double_integrator(n=9)[0]):
-        P = B.Problem(spec)
-        with pytest.raises(B.LspError) as e:
-            B.lsp_adjoint_workspace_size(P.grid, P.opts, 4, 0)
-        assert e.value.status == B.LSP_EUNSUPPORTED

@@ -1,6 +1,8 @@
 """Pins of the oracle's discrete adjoint against central finite differences
 of the FP64 oracle's forward map (fixed step count), in random directions of
-the initial field and the target and along every dynamics parameter."""
+the initial field and the target and along every dynamics parameter (every
+dynamics with state-only LF bounds: the parameters act through H, through
+the GLF coefficients and through dt)."""
 import numpy as np
 import pytest
 
@@ -15,6 +17,14 @@ def _case(kind, scheme):
         spec = W.car4d(n=8, scheme=scheme)[0]
         spec["n"] = [9, 8, 9, 8]
         nsteps = 3
+    elif kind == "rockets":  # Sec. VI-A's game, every axis extrapolated
+        spec = W.rockets(n=12, scheme=scheme, a=1.1, g=30.0, ue=0.9, up=1.2)[0]
+        spec["n"] = [13, 12, 11]
+        nsteps = 4
+    elif kind == "double_integrator":
+        spec = W.double_integrator(n=17, scheme=scheme, umax=0.8)[0]
+        spec["n"] = [17, 15]
+        nsteps = 5
     else:
         spec = W.problem(2, [17, 15], [-1, -1], [1, 1], [False, True], scheme, "normal_speed",
                          [1.3], rk=3, cfl=0.75, tube=True)
@@ -30,7 +40,8 @@ def _J(orc, spec, phi0, g, nsteps, c):
 
 @pytest.mark.parametrize("kind,scheme", [("air3d", "weno5"), ("air3d", "eno3"), ("air3d", "eno2"),
                                          ("air3d", "upwind1"), ("car4d", "eno3"),
-                                         ("normal2d", "weno5")])
+                                         ("normal2d", "weno5"), ("rockets", "eno2"),
+                                         ("rockets", "weno5"), ("double_integrator", "eno2")])
 def test_adjoint_matches_central_differences(orc, kind, scheme):
     spec, phi0, g, nsteps = _case(kind, scheme)
     rng = np.random.default_rng(5)

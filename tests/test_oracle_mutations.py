@@ -85,6 +85,10 @@ ADJOINT_MUTANTS = {
     "adj_tube_branch": ("if (g && g[i] < v) { /* the min took the target */",
                         "if (g && g[i] > v) { /* the min took the target */"),
     "adj_rk3_stage2_weight": ("ln[i] += 0.75 * lb[i];", "ln[i] += 0.25 * lb[i];"),
+    "adj_rockets_dHdp3_sign": ("hp[2] = ue * g1 + up * g2;", "hp[2] = ue * g1 - up * g2;"),
+    "adj_rockets_dHdg_sign": ("hprm[1] = p[1];", "hprm[1] = -p[1];"),
+    "adj_rockets_bound_da": ("g[0] = sgn1(w) * (sin(x[2]) + 1.0);", "g[0] = sgn1(w) * sin(x[2]);"),
+    "adj_double_integrator_dHdp1": ("hp[0] = -x[1];", "hp[0] = x[1];"),
 }
 
 
