@@ -117,6 +117,22 @@ def algorithmic(spec) -> tuple[float, float]:
     return words * word, float(flops)
 
 
+def launch_accounting(spec, tile, stats) -> tuple[int, float, float, bool]:
+    """(stage-kernel launches per solve, algorithmic FLOPs per launch,
+    algorithmic bytes per launch, fused) of a solve with `stats` on `tile`.
+    A fused-RK2 tile (pair 5) runs both stages of a step in one launch, which
+    reads phi (and the target) and writes phi': twice the stage FLOPs and
+    2 or 3 words per node; otherwise one launch per stage."""
+    import numpy as np
+    npts = float(np.prod(spec["n"]))
+    bpn, fpn = algorithmic(spec)
+    fused = bool(tile[0] > 0 and tile[4] == 5 and spec["rk"] == 2)
+    if fused:
+        word = 8 if spec["dtype"] == "f64" else 4
+        return int(stats["steps"]), 2 * fpn * npts, word * (2 + bool(spec.get("tube"))) * npts, True
+    return int(stats["stages"]), fpn * npts, bpn * npts, False
+
+
 KERNEL_SOURCES = ["stencil.cuh", "stage_tiled.cuh", "stage_tiled.inl", "stage_generic.cuh",
                   "pair2.cuh", "stage_pair.cuh", "stage_run.cuh", "stage_run.inl"]
 
@@ -426,16 +442,9 @@ def measure_solve(args, name: str, rank: int, world: int, local_rank: int, clk_t
 
     # ---- roofline of the dominant kernel (the fused stage kernel): its
     # average launch time over the timed region = solve time / stage launches
-    bpn, fpn = algorithmic(spec)
-    fused = tile[0] > 0 and tile[4] == 5 and spec["rk"] == 2
-    launches = stats["steps"] if fused else stages
+    launches, fpl, bpl, fused = launch_accounting(spec, tile, stats)
     per_launch_s = (ms / 1e3) / (launches * args.steps)
-    if fused:  # both RK2 stages per launch: phi (and the target) in, phi' out
-        word = 8 if spec["dtype"] == "f64" else 4
-        roof = roofline_of(2 * fpn * npts, word * (2 + bool(spec.get("tube"))) * npts,
-                           per_launch_s, None)
-    else:
-        roof = roofline_of(fpn * npts, bpn * npts, per_launch_s, measured_traffic(spec["name"]))
+    roof = roofline_of(fpl, bpl, per_launch_s, None if fused else measured_traffic(spec["name"]))
     return {
         "spec": spec, "phi0": phi0, "g": g, "value": value, "ms_per_step": ms / args.steps,
         "config": {"workload": spec["name"], "points": npts, "stages_per_step": stages,

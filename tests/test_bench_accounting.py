@@ -73,3 +73,22 @@ def test_profile_traffic_lines_parse():
                 found += 1
     assert found >= 2
     assert re.fullmatch(r"[0-9a-f]{16}", bench.kernel_hash())
+
+
+def test_launch_accounting_of_fused_rk2_tiles():
+    """A fused-RK2 tile (pair 5) counts one launch per step doing both
+    stages: phi and the target in, phi' out (12 B per node in FP32 with the
+    tube), twice the stage FLOPs; any other tile one launch per stage with
+    the per-stage averages."""
+    spec = W.rockets(n=9)[0]
+    stats = {"steps": 7, "stages": 14}
+    n = 9 ** 3
+    bpn, fpn = bench.algorithmic(spec)
+    launches, f, b, fused = bench.launch_accounting(spec, (16, 16, 4, 2, 5), stats)
+    assert (launches, fused) == (7, True)
+    assert f == pytest.approx(2 * fpn * n) and b == pytest.approx(12 * n)
+    launches, f, b, fused = bench.launch_accounting(spec, (16, 16, 4, 2, 0), stats)
+    assert (launches, fused) == (14, False)
+    assert f == pytest.approx(fpn * n) and b == pytest.approx(bpn * n)
+    spec3 = dict(spec, rk=3)  # pair 5 fuses RK2 steps only
+    assert bench.launch_accounting(spec3, (16, 16, 4, 2, 5), {"steps": 7, "stages": 21})[3] is False
