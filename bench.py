@@ -148,11 +148,12 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(workload_name: str):
+def measured_traffic(workload_name: str, pair: int):
     """dram__bytes_read.sum + dram__bytes_write.sum per stage launch from the
-    committed ncu summary of this workload (profiles/*.md lines
-    `traffic_bytes_per_launch[<workload>]: <bytes> kernel_hash=<hash>`), or
-    None when no summary matches the current kernel sources."""
+    committed ncu summary of this workload and stage-kernel variant (tile
+    pair) (profiles/*.md lines `traffic_bytes_per_launch[<workload>]: <bytes>
+    kernel_hash=<hash> pair=<pair>`), or None when no summary matches the
+    current kernel sources and the variant that ran."""
     import glob
     want = kernel_hash()
     for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
@@ -160,7 +161,8 @@ def measured_traffic(workload_name: str):
             tag = f"traffic_bytes_per_launch[{workload_name}]:"
             if ln.strip().startswith(tag):
                 parts = ln.strip()[len(tag):].split()
-                if len(parts) >= 2 and parts[1] == f"kernel_hash={want}":
+                if (len(parts) >= 3 and parts[1] == f"kernel_hash={want}"
+                        and parts[2] == f"pair={pair}"):
                     return float(parts[0])
     return None
 
@@ -444,7 +446,8 @@ def measure_solve(args, name: str, rank: int, world: int, local_rank: int, clk_t
     # average launch time over the timed region = solve time / stage launches
     launches, fpl, bpl, fused = launch_accounting(spec, tile, stats)
     per_launch_s = (ms / 1e3) / (launches * args.steps)
-    roof = roofline_of(fpl, bpl, per_launch_s, None if fused else measured_traffic(spec["name"]))
+    roof = roofline_of(fpl, bpl, per_launch_s,
+                       None if fused else measured_traffic(spec["name"], int(tile[4])))
     return {
         "spec": spec, "phi0": phi0, "g": g, "value": value, "ms_per_step": ms / args.steps,
         "config": {"workload": spec["name"], "points": npts, "stages_per_step": stages,

@@ -288,7 +288,7 @@ lsp_status lsp_get_tile(const lsp_grid* grid, const lsp_solve_opts* opts, int* t
  * stage alone is timed) for a set of tile shapes (7 fixed, 2 fitted to the
  * grid), chunk lengths, occupancy targets and kernel variants (WENO5: pair 0,
  * 1, 2; ENO2 and ENO3: pair 0, 1, plus the face-shared runs of pairs 3 and
- * 4 on 3 widths x 4 row counts x 7 chunk lengths), re-time the
+ * 4 on 3 widths x 6 row counts x 7 chunk lengths), re-time the
  * six fastest over longer windows and keep the best in the grid handle
  * (reported through tb/ta/ch/minb/pair, which may be NULL).  Waits for the
  * GPU.  For grids without a tiled kernel it selects the generic one (all

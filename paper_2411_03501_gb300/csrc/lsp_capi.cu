@@ -838,23 +838,29 @@ lsp_status lsp_autotune(lsp_grid* g, const lsp_solve_opts* o, const void* phi, v
     // the face-shared ENO runs (pair 3: 4 nodes per thread, pair 4: 2): 16,
     // 28 or 32 nodes of the fastest axis per CTA and 4, 8 or 16 rows, or as
     // many rows as split the second-fastest axis evenly into tiles of at most
-    // 16
-    int run_rows[4] = {4, 8, 16, 0};
+    // 16, 10 or 6 rows (81 nodes: 14, 9 and 6 rows; 9 x 9 rows ran the car4d
+    // stage 5 % faster than 8 or 14)
+    constexpr int kRunRows = 6;
+    int run_rows[kRunRows] = {4, 8, 16, 0, 0, 0};
     {
         const int nA = g->n[d - 2];
-        const int k = (nA + 15) / 16;
-        run_rows[3] = (nA + k - 1) / k;
+        const int target[3] = {16, 10, 6};
+        for (int q = 0; q < 3; ++q) {
+            const int k = (nA + target[q] - 1) / target[q];
+            run_rows[3 + q] = (nA + k - 1) / k;
+        }
     }
     const bool eno = o->scheme == LSP_ENO2 || o->scheme == LSP_ENO3;
-    const int nrun = eno ? 3 * 4 : 0;
+    const int nrun = eno ? 3 * kRunRows : 0;
     for (int si = 0; si < nshapes + nrun; ++si) {
         const bool run = si >= nshapes;
         const int run_tb[3] = {16, 28, 32};
-        const int sh[2] = {run ? run_tb[(si - nshapes) / 4] : shapes[si][0],
-                           run ? run_rows[(si - nshapes) % 4] : shapes[si][1]};
-        if (run && (si - nshapes) % 4 == 3) {
+        const int ri = (si - nshapes) % kRunRows;
+        const int sh[2] = {run ? run_tb[(si - nshapes) / kRunRows] : shapes[si][0],
+                           run ? run_rows[ri] : shapes[si][1]};
+        if (run && ri >= 3) {
             bool dup = false;
-            for (int q = 0; q < 3; ++q) dup |= run_rows[q] == sh[1];
+            for (int q = 0; q < ri; ++q) dup |= run_rows[q] == sh[1];
             if (dup) continue;
         }
         for (int cand = 0; cand < 63; ++cand) {

@@ -60,9 +60,11 @@ def test_roofline_object_picks_the_binding_roof():
 
 def test_profile_traffic_lines_parse():
     """Every traffic line of the committed summaries names a workload, a
-    positive byte count and a 16-hex-digit kernel hash (the benchmark reports
-    the figure only while the kernel sources hash to it)."""
-    pat = re.compile(r"^traffic_bytes_per_launch\[([^\]]+)\]: (\d+) kernel_hash=([0-9a-f]{16})$")
+    positive byte count, a 16-hex-digit kernel hash and the stage-kernel
+    variant (the benchmark reports the figure only while the kernel sources
+    hash to it and that variant ran)."""
+    pat = re.compile(r"^traffic_bytes_per_launch\[([^\]]+)\]: (\d+) kernel_hash=([0-9a-f]{16}) "
+                     r"pair=\d$")
     found = 0
     for f in glob.glob(os.path.join(bench.ROOT, "profiles", "*.md")):
         for ln in open(f):
