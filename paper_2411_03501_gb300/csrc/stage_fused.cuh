@@ -91,6 +91,8 @@ __global__ void __launch_bounds__(256, 2) stage_fused_rk2_kernel(StageArgs<float
 
     // distance of a tile position outside the tile's own nodes along A / B
     auto dist = [](int j, int lo, int hi) { return j < lo ? lo - j : (j > hi ? j - hi : 0); };
+    // one period suffices: positions lie within 2G <= 6 nodes of the grid and
+    // every axis has at least 7 nodes
     auto wrap = [](int j, int n) { return j < 0 ? j + n : (j >= n ? j - n : j); };
 
     // ---- phi tile slots (the node after the wrap of periodic axes): kinds
